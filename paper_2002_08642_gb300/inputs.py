@@ -1,0 +1,146 @@
+"""Seeded synthetic inputs shared by the tests, the oracle checks and the bench.
+
+This module builds inputs only: initial velocity fields, wing meshes, node
+motions and frames. It holds none of the solver's arithmetic (no transform,
+curl, projection, mask profile or force), so that the oracle and the CUDA path
+both receive the same arrays and neither borrows the other's numerics.
+Library routines (numpy's FFT, scipy's Delaunay) are used for synthesis.
+
+Workload recipes (the configurations the solver is exercised on):
+
+* Taylor--Green 3D: u = (sin x cos y cos z, -cos x sin y cos z, 0) on L = 2 pi.
+* Taylor--Green 2D embedded in 3D: u = (sin x cos y, -cos x sin y, 0).
+* Random turbulent-like field: complex Gaussian modes with 1 <= |m| < n/3,
+  shell amplitudes giving E(k) ~ k^(-5/3), scaled so that after the solver's
+  own projection each component has rms ~0.05 (the pre-projection field has
+  rms 0.05 * sqrt(3/2); the projection removes one third of the energy of an
+  isotropic field on average).
+* Flat plate: chord 0.3 (wing x), span 1.0 (wing y), either 2 triangles or a
+  structured nc x ns grid of quads split in two, centred at (2, 2, 2) in an
+  L = 4 box and pitched 30 degrees about the global y axis; static.
+* Elliptic revolving wing: full ellipse with semi-axes 0.175 (chord, wing x)
+  and 0.5 (span, wing y), root at the hinge (wing y = 0), tip at y = 1;
+  ``n_nodes`` nodes (boundary ring + Vogel-spiral interior, Delaunay
+  triangulated); pitched 45 degrees about the span axis and revolving about
+  global z at Omega about the hinge at the box centre. Seeded flapping
+  displacement d_i(t) = a_i sin(2 pi t) along the wing-frame normal with
+  a_i = 0.05 s_i^2 (0.9 + 0.1 zeta_i), zeta_i ~ U[-1, 1], s_i the spanwise
+  coordinate.
+"""
+import math
+
+import numpy as np
+
+
+def grid(n, L):
+    x = np.arange(n) * (L / n)
+    return np.meshgrid(x, x, x, indexing="ij")
+
+
+def taylor_green_3d(n, L=2.0 * math.pi):
+    X, Y, Z = grid(n, L)
+    return np.stack([np.sin(X) * np.cos(Y) * np.cos(Z),
+                     -np.cos(X) * np.sin(Y) * np.cos(Z),
+                     np.zeros_like(X)])
+
+
+def taylor_green_2d(n, L=2.0 * math.pi):
+    X, Y, Z = grid(n, L)
+    return np.stack([np.sin(X) * np.cos(Y),
+                     -np.cos(X) * np.sin(Y),
+                     np.zeros_like(X)])
+
+
+def random_field(n, L, seed=1234, rms=0.05, slope=-5.0 / 3.0):
+    """Band-limited Gaussian random vector field (not yet solenoidal)."""
+    rng = np.random.default_rng(seed)
+    m = np.fft.fftfreq(n, 1.0 / n)
+    mz = np.arange(n // 2 + 1)
+    MX, MY, MZ = np.meshgrid(m, m, mz, indexing="ij")
+    mag = np.sqrt(MX ** 2 + MY ** 2 + MZ ** 2)
+    band = (mag >= 1.0) & (mag < n / 3.0)
+    # E(k) dk ~ k^slope with ~k^2 modes per shell: |a|^2 ~ k^(slope-2)
+    amp = np.where(band, np.power(np.where(band, mag, 1.0), 0.5 * (slope - 2.0)), 0.0)
+    u = np.empty((3, n, n, n))
+    for c in range(3):
+        z = rng.standard_normal(amp.shape) + 1j * rng.standard_normal(amp.shape)
+        u[c] = np.fft.irfftn(z * amp, s=(n, n, n), axes=(0, 1, 2))
+    target = rms * math.sqrt(1.5)
+    for c in range(3):
+        u[c] *= target / np.sqrt(np.mean(u[c] ** 2))
+    return u
+
+
+def rot_y(deg):
+    a = math.radians(deg)
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def rot_z(rad):
+    c, s = math.cos(rad), math.sin(rad)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def frame(R, X_O, V_O=(0.0, 0.0, 0.0), Omega=(0.0, 0.0, 0.0)):
+    return {"R": np.asarray(R, dtype=np.float64).reshape(9),
+            "X_O": np.asarray(X_O, dtype=np.float64),
+            "V_O": np.asarray(V_O, dtype=np.float64),
+            "Omega": np.asarray(Omega, dtype=np.float64)}
+
+
+def plate(chord=0.3, span=1.0, nc=1, ns=1, centre=(2.0, 2.0, 2.0), pitch_deg=30.0):
+    """Static flat plate: wing-frame nodes, zero velocities, triangles, frame."""
+    xs = np.linspace(-0.5 * chord, 0.5 * chord, nc + 1)
+    ys = np.linspace(-0.5 * span, 0.5 * span, ns + 1)
+    XX, YY = np.meshgrid(xs, ys, indexing="ij")
+    xw = np.stack([XX.ravel(), YY.ravel(), np.zeros(XX.size)], axis=1)
+    tri = []
+    for i in range(nc):
+        for j in range(ns):
+            a = i * (ns + 1) + j
+            b = (i + 1) * (ns + 1) + j
+            tri.append((a, b, b + 1))
+            tri.append((a, b + 1, a + 1))
+    tri = np.asarray(tri, dtype=np.int32)
+    vw = np.zeros_like(xw)
+    return xw, vw, tri, frame(rot_y(pitch_deg), centre)
+
+
+def elliptic_wing_mesh(n_nodes=600, half_chord=0.175, half_span=0.5):
+    """Wing-frame nodes (z = 0) and Delaunay triangles of the ellipse."""
+    from scipy.spatial import Delaunay
+
+    n_b = max(16, int(round(2.2 * math.sqrt(n_nodes))))
+    n_i = n_nodes - n_b
+    th = 2.0 * math.pi * np.arange(n_b) / n_b
+    bx = half_chord * np.cos(th)
+    by = half_span + half_span * np.sin(th)
+    golden = math.pi * (3.0 - math.sqrt(5.0))
+    k = np.arange(n_i) + 0.5
+    r = 0.93 * np.sqrt(k / n_i)
+    ang = golden * k
+    ix = half_chord * r * np.cos(ang)
+    iy = half_span + half_span * r * np.sin(ang)
+    x = np.concatenate([bx, ix])
+    y = np.concatenate([by, iy])
+    pts = np.stack([x, y], axis=1)
+    tri = Delaunay(pts).simplices.astype(np.int32)
+    xw = np.stack([x, y, np.zeros_like(x)], axis=1)
+    return xw, tri
+
+
+def flapping_amplitudes(xw, seed=42, amp=0.05):
+    rng = np.random.default_rng(seed)
+    zeta = rng.uniform(-1.0, 1.0, size=xw.shape[0])
+    s = xw[:, 1]
+    return amp * s * s * (0.9 + 0.1 * zeta)
+
+
+def revolving_wing(t, xw0, a, centre=(2.0, 2.0, 2.0), omega=1.0, pitch_deg=45.0):
+    """Node positions/velocities in the wing frame and the frame at time t."""
+    normal = np.array([0.0, 0.0, 1.0])
+    xw = xw0 + (a * math.sin(2.0 * math.pi * t))[:, None] * normal[None]
+    vw = (a * 2.0 * math.pi * math.cos(2.0 * math.pi * t))[:, None] * normal[None]
+    R = rot_z(omega * t) @ rot_y(pitch_deg)
+    return xw, vw, frame(R, centre, (0.0, 0.0, 0.0), (0.0, 0.0, omega))
