@@ -1,0 +1,349 @@
+"""Benchmark of the penalized pseudo-spectral step (Sec. 4.1) on one GB300.
+
+One step = rasterise the wing mask and solid velocity from the node
+positions of that step (Sec. 4.1, Eq. mask_function / relative_velocities)
++ one integrating-factor AB2 step of the penalized Navier--Stokes equations
+with the FP64 force/moment reduction. Metric: Mpts*steps/s = n^3 * steps /
+seconds. Inputs are synthetic (seeded revolving elliptic wing, see
+paper_2002_08642_gb300/inputs.py) and resident in HBM before timing; the
+fields (tens of GB) are far larger than the 129 MB L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+(test infrastructure, the only other use of ``oracle/`` here) on a bounded
+sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # revolving flexible elliptic wing, FP32 bulk, mask rasterised every step
+    "wing768": dict(n=768, L=4.0, nodes=2000, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
+    "wing256": dict(n=256, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
+    "wing128": dict(n=128, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
+}
+
+CPU_SAMPLE_N = 48
+
+
+def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4):
+    """Bytes each pass must move per step with the 2/3-truncated storage
+    (reads + writes of the kept modes only), keyed by pass name."""
+    mm = (n - 1) // 3
+    K, Kz = 2 * mm + 1, mm + 1
+    kk = K * K * Kz
+    nk = n * K * Kz
+    nn = n * n * Kz
+    e = elem_complex
+    mask = flagged_lines * n * 4 * elem_real + n * n  # chi + u_s on flagged lines, flags
+    return {
+        "x_inverse_curl": (3 * kk + 6 * nk) * e,
+        "y_inverse": (6 * nk + 6 * nn) * e,
+        "z_c2r_nonlinear_r2c": (6 * nn + 3 * nn) * e + mask,
+        "y_forward": (3 * nn + 3 * nk) * e,
+        "x_forward_project_ab2": (3 * nk + 3 * kk + 3 * kk + 6 * kk) * e,
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def wing_inputs(cfg, steps):
+    from paper_2002_08642_gb300 import inputs
+
+    xw0, tri = inputs.elliptic_wing_mesh(cfg["nodes"])
+    amp = inputs.flapping_amplitudes(xw0)
+    seq = [inputs.revolving_wing(k * cfg["dt"], xw0, amp) for k in range(steps)]
+    return tri, seq
+
+
+def cpu_oracle_rate(cfg, budget_s=12.0):
+    """The oracle stepping the same workload recipe at CPU_SAMPLE_N^3 for about
+    budget_s seconds: (Mpts*steps/s, steps, n)."""
+    from oracle import mask as OM
+    from oracle import step as S
+    from paper_2002_08642_gb300 import inputs
+
+    n, L = CPU_SAMPLE_N, cfg["L"]
+    dx = L / n
+    o = S.Solver(S.Params(n=n, L=L, nu=cfg["nu"], eta=cfg["eta"], dt=cfg["dt"], x0=(L / 2,) * 3))
+    o.set_velocity(inputs.random_field(n, L, seed=1234))
+    tri, seq = wing_inputs(cfg, 64)
+    t0 = time.perf_counter()
+    k = 0
+    while k < 2 or (time.perf_counter() - t0 < budget_s and k < len(seq)):
+        xw, vw, fr = seq[k]
+        chi, us, _, _ = OM.rasterise(n, L, xw, vw, tri, fr, 2 * dx, 1.5 * dx)
+        o.set_mask(chi, us)
+        o.step(1)
+        k += 1
+    el = time.perf_counter() - t0
+    return n ** 3 * k / el / 1e6, k, n
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(cfg, budget_s=0.0)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, k, n = cpu_oracle_rate(cfg, budget_s=5.0)
+        rates.append(r)
+    el = time.perf_counter() - t0
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": "Mpts*steps/s", "value": value, "unit": "Mpts*steps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_n": CPU_SAMPLE_N},
+        "cpu_baseline": {"value": value, "unit": "Mpts*steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "FP64 numpy oracle stepping the same revolving-wing recipe at %d^3 "
+                                   "(rasterise + step), ~5 s per bench step" % CPU_SAMPLE_N},
+        "e2e": {"value": value, "unit": "Mpts*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_08642_gb300 import build as pbuild
+    from paper_2002_08642_gb300 import inputs
+    from paper_2002_08642_gb300.solver import Solver
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pbuild.build()
+
+    n, L = cfg["n"], cfg["L"]
+    total = args.warmup + args.steps
+    tri, seq = wing_inputs(cfg, total + args.steps)
+    g = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision=cfg["precision"], device=dev)
+    u0 = inputs.random_field(n, L, seed=1234 + rank) if n <= 256 else None
+    if u0 is None:
+        u = torch.zeros((3, n, n, n), dtype=g.dtype, device=dev)
+    else:
+        u = torch.from_numpy(u0).to(dev, g.dtype)
+    g.set_velocity(u)
+    del u
+    tri_d = torch.from_numpy(tri).to(dev, torch.int32)
+    xw_d = [torch.from_numpy(s[0]).to(dev, torch.float64) for s in seq[:total]]
+    vw_d = [torch.from_numpy(s[1]).to(dev, torch.float64) for s in seq[:total]]
+    frames = [s[2] for s in seq]
+
+    def one(k):
+        g.set_mask_from_nodes(xw_d[k], vw_d[k], tri_d, frames[k])
+        g.step(1)
+
+    for k in range(args.warmup):
+        one(k)
+    torch.cuda.synchronize()
+    flagged = int(g.mask()[0].reshape(n * n, n).gt(0).any(dim=1).sum().item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-timed region
+    clocks = Clocks(local)
+    clocks.start()
+    g.timing(True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.warmup, total):
+        one(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    passes = g.timing_read()
+    g.timing(False)
+    clk = clocks.stop()
+    F, M = g.forces()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n ** 3 * args.steps * world / (ms / 1e3) / 1e6
+
+    # ---- end to end through the public API with host buffers
+    xw_h = [torch.from_numpy(s[0]).pin_memory() for s in seq[total:total + args.steps]]
+    vw_h = [torch.from_numpy(s[1]).pin_memory() for s in seq[total:total + args.steps]]
+    fr_h = frames[total:total + args.steps]
+    xw_s = torch.empty_like(xw_d[0])
+    vw_s = torch.empty_like(vw_d[0])
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        xw_s.copy_(xw_h[k], non_blocking=True)
+        vw_s.copy_(vw_h[k], non_blocking=True)
+        g.set_mask_from_nodes(xw_s, vw_s, tri_d, fr_h[k])
+        g.step(1)
+        g.forces()  # device -> host read of F, M (synchronises)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = n ** 3 * args.steps * world / e2e_s / 1e6
+    h2d = 2 * xw_h[0].numel() * 8
+    d2h = 6 * 8
+
+    # ---- roofline of the dominant pass
+    ab = algorithmic_bytes(n, 8 if cfg["precision"] == "fp32" else 16, flagged,
+                           4 if cfg["precision"] == "fp32" else 8)
+    fft_passes = {k: v for k, v in passes.items() if k in ab}
+    top = max(fft_passes, key=lambda k: fft_passes[k][0])
+    tms, tl = fft_passes[top]
+    peak, src = peaks()
+    achieved = ab[top] / (tms / tl / 1e3) / 1e9
+    step_bytes = sum(ab.values())
+    kernels_per_step = 5 + 6
+    out = {
+        "metric": "Mpts*steps/s", "value": value, "unit": "Mpts*steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "L": L, "nodes": cfg["nodes"],
+                   "precision": cfg["precision"], "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": src, "traffic": None,
+                     "algorithmic_bytes_per_launch": ab[top]},
+        "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                          "achieved_GBs": step_bytes / (ms / args.steps / 1e3) / 1e9},
+        "passes_ms": {k: v[0] / max(v[1], 1) for k, v in passes.items()},
+        "e2e": {"value": e2e, "unit": "Mpts*steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": kernels_per_step * args.steps,
+        "forces_last": {"F": F, "M": M},
+    }
+    if clk:
+        out["clocks"] = clk
+    if args.fp64 and world == 1:
+        del g
+        torch.cuda.empty_cache()
+        g64 = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision="fp64", device=dev)
+        g64.set_velocity(torch.zeros((3, n, n, n), dtype=torch.float64, device=dev))
+        k64 = max(2, args.steps // 4)
+        for k in range(2):
+            g64.set_mask_from_nodes(xw_d[k], vw_d[k], tri_d, frames[k])
+            g64.step(1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(k64):
+            g64.set_mask_from_nodes(xw_d[k], vw_d[k], tri_d, frames[k])
+            g64.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        v64 = n ** 3 * k64 / (ms64 / 1e3) / 1e6
+        out["fp64_step"] = {"value": v64, "unit": "Mpts*steps/s", "steps": k64, "ms_per_step": ms64 / k64,
+                            "fp32_speedup": value / v64}
+    if rank == 0 and args.cpu_baseline:
+        r, k, cn = cpu_oracle_rate(cfg)
+        out["cpu_baseline"] = {"value": r, "unit": "Mpts*steps/s", "cores": 1, "kind": "oracle",
+                               "sample": "FP64 numpy oracle, same revolving-wing recipe at %d^3, "
+                                         "%d steps (rasterise + step), single-threaded numpy" % (cn, k)}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wing768", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * ps.h -- C ABI of libps: the GPU time step of the penalized pseudo-spectral
+ * Navier--Stokes solver (Truong, Engels, Kolomenskiy, Schneider, "A mass-spring
+ * fluid-structure interaction solver: application to flexible revolving
+ * wings", Sec. 4.1), its wing mask rasteriser, force/moment reductions and
+ * discrete adjoint.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns a ps_status; PS_OK is 0. On failure the context keeps
+ *   a message readable with ps_last_error(). The library never prints, never
+ *   exits and never frees memory it did not allocate.
+ * - Device pointers ("_dev") are caller-owned CUDA device memory on the
+ *   device the context was created on, densely packed, in the layout stated
+ *   at each call. Host pointers are plain host memory.
+ * - Real-valued device arrays use the context's precision: float for
+ *   PS_FP32, double for PS_FP64 ("real" below). Force, moment, diagnostics,
+ *   node coordinates and frames are always double.
+ * - Physical fields are C-order [ix][iy][iz] (z fastest), n^3 values per
+ *   component, components stored one after another (3*n^3 for a vector).
+ * - The context allocates NO device memory: the caller passes one workspace
+ *   of ps_workspace_size() bytes (256-byte aligned) to ps_init and keeps it
+ *   alive until ps_destroy.
+ * - Work is enqueued on the CUDA stream given to ps_init and is
+ *   asynchronous unless a call says it synchronises. Asynchronous CUDA
+ *   errors surface as PS_ECUDA at the next synchronising call.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ps_ctx ps_ctx;
+
+typedef enum {
+    PS_OK = 0,
+    PS_EINVAL = 1,        /* bad argument (null pointer, size, value)          */
+    PS_ENOMEM = 2,        /* workspace too small                               */
+    PS_ECUDA = 3,         /* a CUDA call or kernel failed                      */
+    PS_ESTATE = 4,        /* call not valid in the context's current state     */
+    PS_EUNSUPPORTED = 5,  /* grid size or option not built into this library   */
+    PS_ENUMERIC = 6       /* a NaN or Inf was found by a diagnostic reduction  */
+} ps_status;
+
+enum { PS_FP32 = 0, PS_FP64 = 1 };
+enum { PS_MASK_COS = 0, PS_MASK_TANH = 1 };
+enum { PS_MEAN_FIXED = 0, PS_MEAN_FREE = 1 };
+
+/*
+ * Solver parameters (Sec. 4.1, Eq. penalized Navier--Stokes; the paper's
+ * C_eta is eta here).
+ *   n          points per axis of the periodic n^3 grid on [0, L)^3; the
+ *              library supports the sizes listed by ps_supported_n().
+ *   precision  PS_FP32: transforms, nonlinear term, projection and update in
+ *              float, force/moment/diagnostic reductions in double;
+ *              PS_FP64: everything in double.
+ *   mask_profile  profile used by ps_set_mask_from_nodes: PS_MASK_COS is
+ *              Sec. 4.1 Eq. (mask_function) (banded, chi = 0 beyond t_w + h);
+ *              PS_MASK_TANH is chi = (1 - tanh((delta - t_w)/h))/2 at every
+ *              grid point.
+ *   mean_mode  PS_MEAN_FIXED: the k = 0 mode of the right-hand side is
+ *              dropped (mean velocity fixed); PS_MEAN_FREE: kept.
+ *   L, nu, eta, dt  box length, kinematic viscosity, penalization constant,
+ *              time step (all > 0).
+ *   tw, h      wing semi-thickness and smoothing semi-width of the mask.
+ *   x0         reference point of the moment.
+ */
+typedef struct {
+    int32_t n;
+    int32_t precision;
+    int32_t mask_profile;
+    int32_t mean_mode;
+    double L, nu, eta, dt;
+    double tw, h;
+    double x0[3];
+} ps_params;
+
+/* Wing frame -> global frame (Sec. 4.1, Eq. relative_velocities):
+ * R row-major 3x3 rotation (global = X_O + R x_wing), X_O origin,
+ * V_O translational velocity, Omega angular velocity. */
+typedef struct {
+    double R[9];
+    double X_O[3];
+    double V_O[3];
+    double Omega[3];
+} ps_frame;
+
+/* Writes up to `cap` supported grid sizes to `out` and the total count to
+ * *count (out may be NULL to query the count). */
+ps_status ps_supported_n(int32_t* out, int32_t cap, int32_t* count);
+
+/* Bytes of device workspace a context with these parameters needs. */
+ps_status ps_workspace_size(const ps_params* p, size_t* bytes);
+
+/* Create a context on the current CUDA device. cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream). workspace_dev must hold
+ * ps_workspace_size() bytes; the context zeroes it (velocity and mask start
+ * at zero). Returns PS_EUNSUPPORTED for a grid size that is not built in. */
+ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev,
+                  size_t workspace_bytes, ps_ctx** out);
+ps_status ps_destroy(ps_ctx* ctx);
+
+/* Velocity u (3*n^3 real, physical, caller device memory). ps_set_velocity
+ * transforms it, truncates it by the 2/3 rule and projects it onto
+ * divergence-free fields (mean kept); the Adams--Bashforth history restarts,
+ * so the next step is an integrating-factor Euler step. ps_get_velocity
+ * writes the current velocity back to physical space. */
+ps_status ps_set_velocity(ps_ctx* ctx, const void* u_dev);
+ps_status ps_get_velocity(ps_ctx* ctx, void* u_dev_out);
+
+/* Dense mask chi (n^3 real in [0,1]) and solid velocity u_s (3*n^3 real),
+ * caller device memory, copied into the workspace (Sec. 4.1: chi and u_s of
+ * the penalization term). */
+ps_status ps_set_mask(ps_ctx* ctx, const void* chi_dev, const void* us_dev);
+
+/* Copy the current mask chi (n^3 real) and solid velocity u_s (3*n^3 real)
+ * into caller device memory. */
+ps_status ps_get_mask(ps_ctx* ctx, void* chi_dev_out, void* us_dev_out);
+
+/* Rasterise chi and u_s from the wing's triangle mesh (Sec. 4.1,
+ * Eq. mask_function, the bounding-box-limited distance to the triangles,
+ * barycentric velocity on the closest triangle, Eq. relative_velocities).
+ *   xw_dev, vw_dev  n_nodes x 3 double: wing-frame node positions/velocities
+ *   tri_dev         n_tri x 3 int32 vertex indices (0-based)
+ *   frame           host pointer, wing -> global frame
+ * Ties in distance go to the smallest triangle index. Where chi = 0, u_s = 0
+ * (PS_MASK_COS); with PS_MASK_TANH every point is evaluated. */
+ps_status ps_set_mask_from_nodes(ps_ctx* ctx, const double* xw_dev, const double* vw_dev,
+                                 int32_t n_nodes, const int32_t* tri_dev, int32_t n_tri,
+                                 const ps_frame* frame);
+
+/* Advance nsteps time steps (Sec. 4.1: u^n -> u^{n+1} with chi^n, u_s^n):
+ * integrating-factor AB2, the first step after ps_set_velocity being
+ * integrating-factor Euler. Asynchronous. */
+ps_status ps_step(ps_ctx* ctx, int32_t nsteps);
+
+/* Penalization force and moment on the solid, F = (dx^3/eta) sum chi (u - u_s),
+ * M = (dx^3/eta) sum (x - x0) x chi (u - u_s), of the velocity at the start of
+ * the last step taken (Sec. 4.2.2 defines lift and drag from this force).
+ * Host outputs; synchronises the stream. */
+ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
+
+/* Kinetic energy (1/2) int |u|^2 dV and max_k |k . c_k| of the current state
+ * (c_k the Fourier coefficients), in double. Host outputs; synchronises.
+ * Returns PS_ENUMERIC (and still writes the values) if the state holds a
+ * NaN or Inf. */
+ps_status ps_diagnostics(ps_ctx* ctx, double* energy, double* max_div);
+
+/* Checkpoint of the time-stepping state (spectral velocity, AB2 history,
+ * step counter) to/from caller device memory of ps_state_size() bytes. */
+ps_status ps_state_size(const ps_ctx* ctx, size_t* bytes);
+ps_status ps_save_state(ps_ctx* ctx, void* buf_dev);
+ps_status ps_restore_state(ps_ctx* ctx, const void* buf_dev);
+
+/* Per-pass device timing with CUDA events on the context's stream.
+ * ps_timing_enable(ctx, 1) resets the accumulators and records events around
+ * each pass of every following ps_step (and around ps_set_mask_from_nodes)
+ * for up to 1024 calls; 0 stops recording. ps_timing_read synchronises and
+ * writes, for each of *count passes (named by ps_timing_name(i)), the summed
+ * milliseconds and the number of timed launches. With ms or launches NULL or
+ * cap too small it only sets *count. */
+ps_status ps_timing_enable(ps_ctx* ctx, int32_t on);
+ps_status ps_timing_read(ps_ctx* ctx, double* ms, int64_t* launches, int32_t cap, int32_t* count);
+const char* ps_timing_name(int32_t i);
+
+/* Text of the last error on this context ("" if none). */
+const char* ps_last_error(const ps_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PS_H */

@@ -1,0 +1,121 @@
+// ps_engine.cuh -- per-(precision, grid size) launch sequences of the step
+// and of the physical <-> spectral conversions, behind a small table of
+// function pointers so that the C ABI can dispatch on the runtime grid size.
+#pragma once
+#include "ps_kernels.cuh"
+
+namespace ps {
+
+struct Bufs {
+    void* U;
+    void* H;
+    void* A;
+    void* B;
+    void* chi;
+    void* us;
+    uint8_t* flag;
+    void* tw;        // twiddle table of the x/y/z lines (complex T)
+    void* Ex;        // exp(-nu kx^2 dt) for the K x/y modes (T)
+    void* Ez;        // exp(-nu kz^2 dt) for the Kz z modes (T)
+    double* partial; // per-block partial sums
+};
+
+struct Ops {
+    int n, C, C5, LY, G;
+    int zblocks;  // blocks of the z pass (= number of force partials)
+    cudaError_t (*prepare)();
+    // ev (nullable): 6 events recorded before pass 1 and after each pass
+    cudaError_t (*step)(const KP&, const Bufs&, int first, cudaStream_t, cudaEvent_t* ev);
+    cudaError_t (*set_velocity)(const KP&, const Bufs&, const void* u, cudaStream_t);
+    cudaError_t (*get_velocity)(const KP&, const Bufs&, void* u, cudaStream_t);
+};
+
+template <typename T, int N> struct Engine {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    static constexpr size_t tw_bytes = (size_t)GE::tw_n * sizeof(C2);
+    static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
+    static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
+    static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2);
+    static constexpr int thr_s = GE::C * GE::G;
+    static constexpr int thr_5 = GE::C5 * GE::G;
+    static constexpr int thr_z = GE::LY * GE::G;
+
+    template <class K> static cudaError_t attr(K k, size_t bytes) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+
+    static cudaError_t prepare() {
+        cudaError_t e;
+        if ((e = attr(k_xinv<T, N, 6>, sm_strided))) return e;
+        if ((e = attr(k_xinv<T, N, 3>, sm_strided))) return e;
+        if ((e = attr(k_yinv<T, N, 6>, sm_strided))) return e;
+        if ((e = attr(k_yinv<T, N, 3>, sm_strided))) return e;
+        if ((e = attr(k_yfwd<T, N>, sm_strided))) return e;
+        if ((e = attr(k_zpass<T, N>, sm_z))) return e;
+        if ((e = attr(k_zfwd_phys<T, N>, sm_z))) return e;
+        if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
+        if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
+        if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
+        return cudaSuccess;
+    }
+
+    static dim3 grid_xs(const KP& kp, int C) { return dim3(kp.Kzp / C, kp.K); }
+    static dim3 grid_ys(const KP& kp) { return dim3(kp.Kzp / GE::C, N); }
+    static int zblocks() { return N * N / GE::LY; }
+
+    static cudaError_t step(const KP& kp, const Bufs& b, int first, cudaStream_t s, cudaEvent_t* ev) {
+        const C2* tw = (const C2*)b.tw;
+        if (ev) cudaEventRecord(ev[0], s);
+        k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
+        if (ev) cudaEventRecord(ev[1], s);
+        k_yinv<T, N, 6><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
+        if (ev) cudaEventRecord(ev[2], s);
+        k_zpass<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+                                                     b.flag, b.partial, tw);
+        if (ev) cudaEventRecord(ev[3], s);
+        k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
+        if (ev) cudaEventRecord(ev[4], s);
+        k_xfwd<T, N, 0><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
+                                                                 (const T*)b.Ex, (const T*)b.Ez, first, tw);
+        if (ev) cudaEventRecord(ev[5], s);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t set_velocity(const KP& kp, const Bufs& b, const void* u, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, tw);
+        k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
+        k_xfwd<T, N, 1><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
+                                                                 (const T*)b.Ex, (const T*)b.Ez, 0, tw);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t get_velocity(const KP& kp, const Bufs& b, void* u, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
+        k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
+        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)u, tw);
+        return cudaGetLastError();
+    }
+
+    static Ops ops() {
+        Ops o;
+        o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
+        o.zblocks = zblocks();
+        o.prepare = &prepare;
+        o.step = &step;
+        o.set_velocity = &set_velocity;
+        o.get_velocity = &get_velocity;
+        return o;
+    }
+};
+
+// Grid sizes built into the library.
+#define PS_SIZES(X) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+
+// Defined in the per-precision translation units.
+const Ops* ops_f32(int n);
+const Ops* ops_f64(int n);
+
+}  // namespace ps

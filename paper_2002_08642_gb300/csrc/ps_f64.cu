@@ -1,0 +1,19 @@
+// ps_f64.cu -- double instantiations of the step engine for every built-in grid size.
+#include "ps_engine.cuh"
+
+namespace ps {
+
+#define PS_OPS_ENTRY(n)                                  \
+    case n: {                                            \
+        static const Ops o = Engine<double, n>::ops();       \
+        return &o;                                       \
+    }
+
+const Ops* ops_f64(int n) {
+    switch (n) {
+        PS_SIZES(PS_OPS_ENTRY)
+        default: return nullptr;
+    }
+}
+
+}  // namespace ps

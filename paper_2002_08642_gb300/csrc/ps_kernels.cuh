@@ -1,0 +1,525 @@
+// ps_kernels.cuh -- the transform passes and fused pointwise kernels of one
+// time step of the penalized pseudo-spectral Navier--Stokes solver
+// (Sec. 4.1, Eq. penalized Navier--Stokes; time stepping paragraph).
+//
+// Storage (element = complex T unless stated):
+//   U, H   spectral velocity c_k = DFT(u)_k / n^3 and AB2 history N^{n-1},
+//          3 x [K][K][Kzp], only the modes the 2/3 rule keeps:
+//          x/y index c in [0, K) <-> mode m = c (c <= mmax) or c - K,
+//          z index c in [0, Kz) <-> mode m = c; K = 2 mmax + 1, Kz = mmax + 1,
+//          mmax = (n - 1) / 3, Kzp = Kz rounded up to the tile width.
+//   A      after the x transform: nf x [n][K][Kzp]   (x physical, y/z spectral)
+//   B      after the y transform: nf x [n][n][Kzp]   (x/y physical, z spectral)
+//   chi    n^3 real, us 3 x n^3 real, line flag [n][n] (1 if the z line
+//          touches chi > 0)
+// Every aliased mode is identically zero, so the passes never read or write
+// it: the x pass reads K of n rows, the y pass K of n rows, and the z pass
+// Kz of n/2+1 entries per line.
+//
+// Pass order of a step (P = Leray projection, E = exp(-nu |k|^2 dt)):
+//   1 x-inverse of u_hat and omega_hat = i k x u_hat (curl fused)    U -> A (6)
+//   2 y-inverse                                                      A -> B (6)
+//   3 z c2r, n = u x omega - (chi/eta)(u - u_s), force/moment partial
+//     sums in double, z r2c truncated to Kz                          B -> B (3)
+//   4 y-forward truncated to K rows                                  B -> A (3)
+//   5 x-forward truncated to K rows, 1/n^3, P, integrating-factor
+//     AB2 (Euler on the first step)                                  A,U,H -> U,H
+#pragma once
+#include "ps_fft.cuh"
+
+namespace ps {
+
+struct KP {
+    int mmax, K, Kz, Kzp;
+    double ks;        // 2 pi / L
+    double dt, inv_eta, invn3, dx, half_L3;
+    double x0[3];
+    int mean_free;
+};
+
+__device__ __forceinline__ int mode_of(int q, int n) { return q < n / 2 ? q : q - n; }
+__device__ __forceinline__ int cidx_of(int m, int K) { return m >= 0 ? m : m + K; }
+__device__ __forceinline__ int cmode_of(int c, int mmax, int K) { return c <= mmax ? c : c - K; }
+
+// Neumaier-compensated accumulation in double.
+struct Acc {
+    double s, c;
+    __device__ __forceinline__ void add(double v) {
+        double t = s + v;
+        if (fabs(s) >= fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double val() const { return s + c; }
+};
+
+// Block-wide sum of `nv` doubles per thread into out[0..nv) (thread 0 writes).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* out, double* scratch) {
+    for (int i = 0; i < NV; ++i) {
+        double x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        v[i] = x;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+        for (int i = 0; i < NV; ++i) scratch[wid * NV + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += scratch[w * NV + i];
+            out[i] = s;
+        }
+    }
+}
+
+// Launch geometry per (T, n): tile width C of the strided passes (128-byte
+// rows), C5 of the x-forward/update pass (three tiles must fit), LY lines
+// per block of the z pass.
+template <typename T, int N> struct Geo {
+    using C2 = cplx<T>;
+    static constexpr int G = LineFFT<T, N, 1>::G;
+    static constexpr int CW = 128 / (int)sizeof(C2);     // 16 (float), 8 (double)
+    static constexpr int C = CW;
+    static constexpr int C5 = (3 * N * CW * (int)sizeof(C2) <= 110 * 1024) ? CW
+                            : (3 * N * (CW / 2) * (int)sizeof(C2) <= 150 * 1024) ? CW / 2 : CW / 4;
+    static constexpr int LP = N + N / 16;                  // padded z line
+    static constexpr int ly_threads() { int l = 256 / G; return l < 1 ? 1 : l; }
+    static constexpr int ly_smem() {
+        int l = 1;
+        while (l * 2 * 3 * LP * (int)sizeof(C2) <= 64 * 1024) l *= 2;
+        return l;
+    }
+    static constexpr int LYa = ly_threads() < ly_smem() ? ly_threads() : ly_smem();
+    static constexpr int ly_fix(int l) { while (l > 1 && (N * N) % l != 0) l /= 2; return l; }
+    static constexpr int LY = ly_fix(LYa);
+    static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
+};
+
+__device__ __forceinline__ int zaddr(int p, int line, int LP) { return line * LP + p + (p >> 4); }
+
+template <typename C2>
+__device__ __forceinline__ void load_tw(C2* s, const C2* g, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = g[i];
+}
+
+// ---------------------------------------------------------------- pass 1
+// x-inverse of the three velocity components and, if NF == 6, of the
+// vorticity omega_hat = i k x u_hat (components 3..5).
+template <typename T, int N, int NF>
+__global__ void __launch_bounds__(Geo<T, N>::C * Geo<T, N>::G)
+k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int C = GE::C, G = GE::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tile = tw + GE::tw_n;
+    const int col = threadIdx.x % C, g = threadIdx.x / C;
+    const int cz = blockIdx.x * C + col;
+    const bool okz = cz < kp.Kz;
+    const int cy = blockIdx.y;
+    const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
+    const T ky = (T)(kp.ks * cmode_of(cy, mmax, K));
+    const T kz = (T)(kp.ks * cz);
+    const size_t FS = (size_t)K * K * Kzp;
+    const size_t AS = (size_t)N * K * Kzp;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return p * C + col; };
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+        __syncthreads();
+        auto load = [&](int q) -> C2 {
+            const int m = mode_of(q, N);
+            if (!okz || m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
+            const size_t o = ((size_t)cidx_of(m, K) * K + cy) * Kzp + cz;
+            const T kx = (T)(kp.ks * m);
+            if (f < 3) return U[f * FS + o];
+            if (f == 3) {  // i (ky uz - kz uy)
+                C2 uy = U[FS + o], uz = U[2 * FS + o];
+                return cmk<C2>(-(ky * uz.y - kz * uy.y), ky * uz.x - kz * uy.x);
+            }
+            if (f == 4) {  // i (kz ux - kx uz)
+                C2 ux = U[o], uz = U[2 * FS + o];
+                return cmk<C2>(-(kz * ux.y - kx * uz.y), kz * ux.x - kx * uz.x);
+            }
+            C2 ux = U[o], uy = U[FS + o];  // i (kx uy - ky ux)
+            return cmk<C2>(-(kx * uy.y - ky * ux.y), kx * uy.x - ky * ux.x);
+        };
+        auto store = [&](int x, C2 v) {
+            if (okz) A[f * AS + ((size_t)x * K + cy) * Kzp + cz] = v;
+        };
+        LineFFT<T, N, 1>::template run<false>(tile, tw, addr, g, load, store);
+    }
+}
+
+// ---------------------------------------------------------------- pass 2
+template <typename T, int N, int NF>
+__global__ void __launch_bounds__(Geo<T, N>::C * Geo<T, N>::G)
+k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int C = GE::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tile = tw + GE::tw_n;
+    const int col = threadIdx.x % C, g = threadIdx.x / C;
+    const int cz = blockIdx.x * C + col;
+    const bool okz = cz < kp.Kz;
+    const int x = blockIdx.y;
+    const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
+    const size_t AS = (size_t)N * K * Kzp;
+    const size_t BS = (size_t)N * N * Kzp;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return p * C + col; };
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+        __syncthreads();
+        auto load = [&](int q) -> C2 {
+            const int m = mode_of(q, N);
+            if (!okz || m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
+            return A[f * AS + ((size_t)x * K + cidx_of(m, K)) * Kzp + cz];
+        };
+        auto store = [&](int y, C2 v) {
+            if (okz) B[f * BS + ((size_t)x * N + y) * Kzp + cz] = v;
+        };
+        LineFFT<T, N, 1>::template run<false>(tile, tw, addr, g, load, store);
+    }
+}
+
+// ---------------------------------------------------------------- pass 3
+// z lines of (x, y): c2r of six fields as three complex lines
+// (u_x + i u_y, u_z + i w_x, w_y + i w_z), the pointwise nonlinear and
+// penalization term, force/moment partials, r2c of n as (n_x + i n_y) and
+// (n_z + 0 i), truncated to kz < Kz, written over fields 0..2 of B.
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
+k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
+        const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tiles = tw + GE::tw_n;
+    __shared__ double red[32 * 6];
+    const int line = threadIdx.x / G, g = threadIdx.x % G;
+    const long lid = (long)blockIdx.x * LY + line;
+    const int x = (int)(lid / N), y = (int)(lid % N);
+    const int Kz = kp.Kz, Kzp = kp.Kzp;
+    const size_t BS = (size_t)N * N * Kzp;
+    const size_t lo = ((size_t)x * N + y) * Kzp;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return zaddr(p, line, LP); };
+    C2* t0 = tiles;
+    C2* t1 = tiles + LY * LP;
+    C2* t2 = tiles + 2 * LY * LP;
+    __syncthreads();
+#pragma unroll 1
+    for (int pr = 0; pr < 3; ++pr) {
+        C2* tp = tiles + pr * LY * LP;
+        const C2* fa = B + (2 * pr) * BS + lo;
+        const C2* fb = B + (2 * pr + 1) * BS + lo;
+        auto load = [&](int q) -> C2 {
+            if (q < Kz) {
+                C2 a = fa[q], b = fb[q];
+                if (q == 0) { a.y = 0; b.y = 0; }
+                return cmk<C2>(a.x - b.y, a.y + b.x);          // A + i B
+            }
+            if (q > N - Kz) {
+                C2 a = fa[N - q], b = fb[N - q];
+                return cmk<C2>(a.x + b.y, b.x - a.y);          // conj(A) + i conj(B)
+            }
+            return cmk<C2>((T)0, (T)0);
+        };
+        auto store = [&](int p, C2 v) { tp[addr(p)] = v; };
+        LineFFT<T, N, 1>::template run<false>(tp, tw, addr, g, load, store);
+    }
+    __syncthreads();
+    // pointwise: n = u x w - (chi/eta)(u - us); forces in double
+    double fm[6] = {0, 0, 0, 0, 0, 0};
+    const bool has_mask = flag[(size_t)x * N + y] != 0;
+    const size_t po = ((size_t)x * N + y) * N;
+    const size_t N3 = (size_t)N * N * N;
+    const T inv_eta = (T)kp.inv_eta;
+    Acc acc[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int z = g; z < N; z += G) {
+        const int a = addr(z);
+        C2 z0 = t0[a], z1 = t1[a], z2 = t2[a];
+        const T ux = z0.x, uy = z0.y, uz = z1.x, wx = z1.y, wy = z2.x, wz = z2.y;
+        T nx = uy * wz - uz * wy;
+        T ny = uz * wx - ux * wz;
+        T nz = ux * wy - uy * wx;
+        if (has_mask) {
+            const T c = chi[po + z];
+            if (c != (T)0) {
+                const T sx = us[po + z], sy = us[N3 + po + z], sz = us[2 * N3 + po + z];
+                const T ce = c * inv_eta;
+                nx -= ce * (ux - sx);
+                ny -= ce * (uy - sy);
+                nz -= ce * (uz - sz);
+                const double cd = (double)c;
+                const double px = cd * ((double)ux - (double)sx);
+                const double py = cd * ((double)uy - (double)sy);
+                const double pz = cd * ((double)uz - (double)sz);
+                const double rx = x * kp.dx - kp.x0[0], ry = y * kp.dx - kp.x0[1], rz = z * kp.dx - kp.x0[2];
+                acc[0].add(px);
+                acc[1].add(py);
+                acc[2].add(pz);
+                acc[3].add(ry * pz - rz * py);
+                acc[4].add(rz * px - rx * pz);
+                acc[5].add(rx * py - ry * px);
+            }
+        }
+        t0[a] = cmk<C2>(nx, ny);
+        t1[a] = cmk<C2>(nz, (T)0);
+    }
+    for (int i = 0; i < 6; ++i) fm[i] = acc[i].val();
+    __syncthreads();
+#pragma unroll 1
+    for (int pr = 0; pr < 2; ++pr) {
+        C2* tp = tiles + pr * LY * LP;
+        auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
+        auto store = [&](int p, C2 v) { tp[addr(p)] = v; };
+        LineFFT<T, N, -1>::template run<true>(tp, tw, addr, g, noload, store);
+        __syncthreads();
+    }
+    // unpack the two-for-one transform, keep kz < Kz
+    C2* o0 = B + lo;
+    C2* o1 = B + BS + lo;
+    C2* o2 = B + 2 * BS + lo;
+    for (int k = g; k < Kz; k += G) {
+        const C2 zk = t0[addr(k)];
+        const C2 zm = t0[addr((N - k) % N)];
+        // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
+        o0[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+        o1[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+        o2[k] = t1[addr(k)];
+    }
+    block_sum<6>(fm, partial + (size_t)blockIdx.x * 6, red);
+}
+
+// ---------------------------------------------------------------- pass 4
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::C * Geo<T, N>::G)
+k_yfwd(KP kp, const cplx<T>* __restrict__ B, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int C = GE::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tile = tw + GE::tw_n;
+    const int col = threadIdx.x % C, g = threadIdx.x / C;
+    const int cz = blockIdx.x * C + col;
+    const bool okz = cz < kp.Kz;
+    const int x = blockIdx.y;
+    const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
+    const size_t AS = (size_t)N * K * Kzp;
+    const size_t BS = (size_t)N * N * Kzp;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return p * C + col; };
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+        __syncthreads();
+        auto load = [&](int y) -> C2 {
+            if (!okz) return cmk<C2>((T)0, (T)0);
+            return B[f * BS + ((size_t)x * N + y) * Kzp + cz];
+        };
+        auto store = [&](int q, C2 v) {
+            const int m = mode_of(q, N);
+            if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * Kzp + cz] = v;
+        };
+        LineFFT<T, N, -1>::template run<false>(tile, tw, addr, g, load, store);
+    }
+}
+
+// ---------------------------------------------------------------- pass 5
+// MODE 0: time step (Euler if first != 0, else AB2); MODE 1: set velocity
+// (project with the mean kept, history cleared).
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(Geo<T, N>::C5 * Geo<T, N>::G)
+k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H,
+       const T* __restrict__ Ex, const T* __restrict__ Ez, int first, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int C = GE::C5;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tiles = tw + GE::tw_n;
+    const int col = threadIdx.x % C, g = threadIdx.x / C;
+    const int cz0 = blockIdx.x * C;
+    const int cz = cz0 + col;
+    const bool okz = cz < kp.Kz;
+    const int cy = blockIdx.y;
+    const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
+    const size_t AS = (size_t)N * K * Kzp;
+    const size_t FS = (size_t)K * K * Kzp;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return p * C + col; };
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+        C2* tile = tiles + f * N * C;
+        __syncthreads();
+        auto load = [&](int x) -> C2 {
+            if (!okz) return cmk<C2>((T)0, (T)0);
+            return A[f * AS + ((size_t)x * K + cy) * Kzp + cz];
+        };
+        auto store = [&](int q, C2 v) { tile[addr(q)] = v; };
+        LineFFT<T, N, -1>::template run<false>(tile, tw, addr, g, load, store);
+    }
+    __syncthreads();
+    const T s = (T)kp.ks;
+    const T my = (T)cmode_of(cy, mmax, K);
+    const T invn3 = (T)kp.invn3;
+    const T dt = (T)kp.dt;
+    const T ey = Ex[cy];
+    for (int idx = threadIdx.x; idx < K * C; idx += blockDim.x) {
+        const int cx = idx / C, c = idx % C;
+        const int czz = cz0 + c;
+        if (czz >= kp.Kz) continue;
+        const int mx = cmode_of(cx, mmax, K);
+        const int q = mx >= 0 ? mx : mx + N;
+        const int a = q * C + c;
+        C2 n0 = tiles[a], n1 = tiles[N * C + a], n2 = tiles[2 * N * C + a];
+        n0.x *= invn3; n0.y *= invn3;
+        n1.x *= invn3; n1.y *= invn3;
+        n2.x *= invn3; n2.y *= invn3;
+        const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+        const T k2 = kx * kx + ky * ky + kz * kz;
+        const bool zero = (mx == 0 && cy == 0 && czz == 0);
+        if (!zero) {
+            const T ik2 = (T)1 / k2;
+            const T dr = (kx * n0.x + ky * n1.x + kz * n2.x) * ik2;
+            const T di = (kx * n0.y + ky * n1.y + kz * n2.y) * ik2;
+            n0.x -= kx * dr; n0.y -= kx * di;
+            n1.x -= ky * dr; n1.y -= ky * di;
+            n2.x -= kz * dr; n2.y -= kz * di;
+        } else if (MODE == 0 && !kp.mean_free) {
+            n0 = n1 = n2 = cmk<C2>((T)0, (T)0);
+        }
+        const size_t o = ((size_t)cx * K + cy) * Kzp + czz;
+        if constexpr (MODE == 1) {
+            U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
+            const C2 z = cmk<C2>((T)0, (T)0);
+            H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
+        } else {
+            const T E = Ex[cx] * ey * Ez[czz];
+            C2 nn[3] = {n0, n1, n2};
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const C2 u = U[f * FS + o];
+                C2 r;
+                if (first) {
+                    r = cmk<C2>(E * (u.x + dt * nn[f].x), E * (u.y + dt * nn[f].y));
+                } else {
+                    const C2 h = H[f * FS + o];
+                    const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
+                    r = cmk<C2>(E * u.x + a3 * nn[f].x - a2 * h.x, E * u.y + a3 * nn[f].y - a2 * h.y);
+                }
+                U[f * FS + o] = r;
+                H[f * FS + o] = nn[f];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------- physical <-> z-spectral
+// Forward: physical u (3 x n^3 real) -> B fields 0..2 (z r2c, kz < Kz).
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
+k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tiles = tw + GE::tw_n;
+    const int line = threadIdx.x / G, g = threadIdx.x % G;
+    const long lid = (long)blockIdx.x * LY + line;
+    const int x = (int)(lid / N), y = (int)(lid % N);
+    const int Kz = kp.Kz, Kzp = kp.Kzp;
+    const size_t BS = (size_t)N * N * Kzp;
+    const size_t lo = ((size_t)x * N + y) * Kzp;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t po = ((size_t)x * N + y) * N;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return zaddr(p, line, LP); };
+    C2* t0 = tiles;
+    C2* t1 = tiles + LY * LP;
+    __syncthreads();
+    {
+        auto load = [&](int z) -> C2 { return cmk<C2>(u[po + z], u[N3 + po + z]); };
+        auto store = [&](int p, C2 v) { t0[addr(p)] = v; };
+        LineFFT<T, N, -1>::template run<false>(t0, tw, addr, g, load, store);
+    }
+    __syncthreads();
+    {
+        auto load = [&](int z) -> C2 { return cmk<C2>(u[2 * N3 + po + z], (T)0); };
+        auto store = [&](int p, C2 v) { t1[addr(p)] = v; };
+        LineFFT<T, N, -1>::template run<false>(t1, tw, addr, g, load, store);
+    }
+    __syncthreads();
+    C2* o0 = B + lo;
+    C2* o1 = B + BS + lo;
+    C2* o2 = B + 2 * BS + lo;
+    for (int k = g; k < Kz; k += G) {
+        const C2 zk = t0[addr(k)];
+        const C2 zm = t0[addr((N - k) % N)];
+        o0[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+        o1[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+        o2[k] = t1[addr(k)];
+    }
+}
+
+// Inverse: B fields 0..2 (z spectral, kz < Kz) -> physical u (3 x n^3 real).
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
+k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* tw = reinterpret_cast<C2*>(smraw);
+    C2* tiles = tw + GE::tw_n;
+    const int line = threadIdx.x / G, g = threadIdx.x % G;
+    const long lid = (long)blockIdx.x * LY + line;
+    const int x = (int)(lid / N), y = (int)(lid % N);
+    const int Kz = kp.Kz, Kzp = kp.Kzp;
+    const size_t BS = (size_t)N * N * Kzp;
+    const size_t lo = ((size_t)x * N + y) * Kzp;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t po = ((size_t)x * N + y) * N;
+    load_tw(tw, twg, GE::tw_n);
+    auto addr = [&](int p) { return zaddr(p, line, LP); };
+    __syncthreads();
+#pragma unroll 1
+    for (int pr = 0; pr < 2; ++pr) {
+        C2* tp = tiles + pr * LY * LP;
+        const C2* fa = B + (2 * pr) * BS + lo;
+        const C2* fb = B + (2 * pr + 1) * BS + lo;
+        const bool pair = (pr == 0);
+        auto load = [&](int q) -> C2 {
+            if (q < Kz) {
+                C2 a = fa[q];
+                C2 b = pair ? fb[q] : cmk<C2>((T)0, (T)0);
+                if (q == 0) { a.y = 0; b.y = 0; }
+                return cmk<C2>(a.x - b.y, a.y + b.x);
+            }
+            if (q > N - Kz) {
+                C2 a = fa[N - q];
+                C2 b = pair ? fb[N - q] : cmk<C2>((T)0, (T)0);
+                return cmk<C2>(a.x + b.y, b.x - a.y);
+            }
+            return cmk<C2>((T)0, (T)0);
+        };
+        auto store = [&](int z, C2 v) {
+            if (pair) { u[po + z] = v.x; u[N3 + po + z] = v.y; }
+            else u[2 * N3 + po + z] = v.x;
+        };
+        LineFFT<T, N, 1>::template run<false>(tp, tw, addr, g, load, store);
+    }
+}
+
+}  // namespace ps

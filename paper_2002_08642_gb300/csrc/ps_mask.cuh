@@ -1,0 +1,384 @@
+// ps_mask.cuh -- GPU rasteriser of the wing mask chi and the solid velocity
+// u_s from the mass-spring wing's triangle mesh (Sec. 4.1):
+//   * delta(x) = min over triangles of the distance from grid point x to the
+//     triangle, each triangle tested only against the grid points of its
+//     bounding box dilated by t_w + h (the mask's reach; no periodic images);
+//   * chi(delta) by Eq. (mask_function) (or the tanh profile, evaluated at
+//     every point against every triangle);
+//   * u_s = V_O + R (sum_v beta_v v_v^(w)) + Omega x (x - X_O) with beta the
+//     barycentric coordinates of the closest point on the closest triangle
+//     (Eq. relative_velocities).
+//
+// Banded (cosine) profile, per call:
+//   clear     zero chi/u_s and reset the per-point keys of the points the
+//             previous call touched (list kept in the workspace);
+//   nodes     global node positions X_O + R x^(w) (double);
+//   boxes     per-triangle grid-index bounding boxes and an exclusive prefix
+//             sum of their point counts (one block);
+//   scatter1  for every (triangle, box point) pair with distance < reach:
+//             atomicMin of the distance bits (non-negative IEEE values order
+//             like their bit patterns); the first writer appends the point
+//             to the touched list;
+//   scatter2  pairs whose distance equals the minimum bit for bit:
+//             atomicMin of the triangle index (ties -> smallest index);
+//   evaluate  per touched point: distance and barycentrics recomputed in
+//             double on the winning triangle, chi, u_s, line flags.
+// The distance used to pick the winner is computed in the context precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace ps {
+
+struct MaskArgs {
+    int n;
+    double dx, tw, h;
+    int profile;
+    const double* xw;
+    const double* vw;
+    int n_nodes;
+    const int32_t* tri;
+    int n_tri;
+    double R[9], XO[3], VO[3], Om[3];
+};
+
+static constexpr int kMaskMaxTri = 1 << 17;
+static constexpr int kMaskMaxNodes = 1 << 17;
+
+// Workspace: keys (8 B/pt), winner ids (4 B/pt), two touched lists (4 B/pt
+// each), counters, node and triangle scratch.
+inline size_t mask_workspace_bytes(int n) {
+    const size_t n3 = (size_t)n * n * n;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return a(n3 * 8) + a(n3 * 4) + 2 * a(n3 * 4) + a(64) + a((size_t)kMaskMaxNodes * 3 * 8) +
+           a((size_t)kMaskMaxTri * 8 * 4) + a(((size_t)kMaskMaxTri + 1) * 8);
+}
+
+struct MaskWs {
+    unsigned long long* key;
+    int32_t* win;
+    uint32_t* list[2];
+    unsigned long long* cnt;  // [0],[1]: list lengths, [2]: total pairs, [4]: bad-index flag
+    double* xg;
+    int32_t* box;              // per triangle: i0,j0,k0,ei,ej,ek (+2 pad)
+    unsigned long long* pre;   // exclusive prefix of box sizes (n_tri + 1)
+};
+
+inline MaskWs mask_ws_split(unsigned char* w, int n) {
+    const size_t n3 = (size_t)n * n * n;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    MaskWs m;
+    size_t o = 0;
+    m.key = (unsigned long long*)(w + o); o += a(n3 * 8);
+    m.win = (int32_t*)(w + o); o += a(n3 * 4);
+    m.list[0] = (uint32_t*)(w + o); o += a(n3 * 4);
+    m.list[1] = (uint32_t*)(w + o); o += a(n3 * 4);
+    m.cnt = (unsigned long long*)(w + o); o += a(64);
+    m.xg = (double*)(w + o); o += a((size_t)kMaskMaxNodes * 3 * 8);
+    m.box = (int32_t*)(w + o); o += a((size_t)kMaskMaxTri * 8 * 4);
+    m.pre = (unsigned long long*)(w + o);
+    return m;
+}
+
+// Closest point of triangle (a, b, c) to p by Voronoi-region tests on the
+// vertices, edges and face; returns squared distance and barycentrics.
+template <typename R>
+__device__ __forceinline__ R closest_tri(const R p[3], const R a[3], const R b[3], const R c[3], R bary[3]) {
+    R ab[3], ac[3], ap[3], bp[3], cp[3];
+    for (int i = 0; i < 3; ++i) {
+        ab[i] = b[i] - a[i];
+        ac[i] = c[i] - a[i];
+        ap[i] = p[i] - a[i];
+        bp[i] = p[i] - b[i];
+        cp[i] = p[i] - c[i];
+    }
+    auto dot = [](const R* u, const R* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+    const R d1 = dot(ab, ap), d2 = dot(ac, ap);
+    R v, w;
+    if (d1 <= (R)0 && d2 <= (R)0) { v = 0; w = 0; }
+    else {
+        const R d3 = dot(ab, bp), d4 = dot(ac, bp);
+        const R d5 = dot(ab, cp), d6 = dot(ac, cp);
+        const R vc = d1 * d4 - d3 * d2;
+        const R vb = d5 * d2 - d1 * d6;
+        const R va = d3 * d6 - d5 * d4;
+        if (d3 >= (R)0 && d4 <= d3) { v = 1; w = 0; }
+        else if (vc <= (R)0 && d1 >= (R)0 && d3 <= (R)0) { v = d1 / (d1 - d3); w = 0; }
+        else if (d6 >= (R)0 && d5 <= d6) { v = 0; w = 1; }
+        else if (vb <= (R)0 && d2 >= (R)0 && d6 <= (R)0) { v = 0; w = d2 / (d2 - d6); }
+        else if (va <= (R)0 && (d4 - d3) >= (R)0 && (d5 - d6) >= (R)0) {
+            w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+            v = (R)1 - w;
+        } else {
+            const R den = (R)1 / (va + vb + vc);
+            v = vb * den;
+            w = vc * den;
+        }
+    }
+    bary[0] = (R)1 - v - w;
+    bary[1] = v;
+    bary[2] = w;
+    R d2s = 0;
+    for (int i = 0; i < 3; ++i) {
+        const R q = ap[i] - v * ab[i] - w * ac[i];
+        d2s += q * q;
+    }
+    return d2s;
+}
+
+template <typename T> struct KeyBits;
+template <> struct KeyBits<float> {
+    static __device__ __forceinline__ unsigned long long of(float d) { return (unsigned long long)__float_as_uint(d); }
+    static __device__ __forceinline__ float val(unsigned long long k) { return __uint_as_float((unsigned)k); }
+};
+template <> struct KeyBits<double> {
+    static __device__ __forceinline__ unsigned long long of(double d) { return (unsigned long long)__double_as_longlong(d); }
+    static __device__ __forceinline__ double val(unsigned long long k) { return __longlong_as_double((long long)k); }
+};
+
+__global__ void k_mask_clear(MaskWs m, int par, void* chi, void* us, size_t elem, size_t n3) {
+    const unsigned long long cnt = m.cnt[par];
+    const uint32_t* L = m.list[par];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = L[i];
+        m.key[p] = ~0ull;
+        m.win[p] = 0x7fffffff;
+        if (elem == 4) {
+            ((float*)chi)[p] = 0.f;
+            for (int c = 0; c < 3; ++c) ((float*)us)[c * n3 + p] = 0.f;
+        } else {
+            ((double*)chi)[p] = 0.0;
+            for (int c = 0; c < 3; ++c) ((double*)us)[c * n3 + p] = 0.0;
+        }
+    }
+}
+
+__global__ void k_mask_nodes(MaskWs m, MaskArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_nodes) return;
+    for (int r = 0; r < 3; ++r) {
+        double s = a.XO[r];
+        for (int c = 0; c < 3; ++c) s += a.R[3 * r + c] * a.xw[3 * i + c];
+        m.xg[3 * i + r] = s;
+    }
+}
+
+// One block: boxes and their exclusive prefix sum (sequential chunks per
+// thread, then a serial pass over the chunk totals).
+__global__ void k_mask_boxes(MaskWs m, MaskArgs a, double reach) {
+    __shared__ unsigned long long part[1024];
+    const int nt = a.n_tri;
+    const int per = (nt + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
+    unsigned long long local = 0;
+    for (int t = t0; t < t1; ++t) {
+        int ok = 1;
+        double lo[3], hi[3];
+        for (int r = 0; r < 3; ++r) { lo[r] = 1e300; hi[r] = -1e300; }
+        for (int v = 0; v < 3; ++v) {
+            const int id = a.tri[3 * t + v];
+            if (id < 0 || id >= a.n_nodes) { ok = 0; break; }
+            for (int r = 0; r < 3; ++r) {
+                const double q = m.xg[3 * id + r];
+                lo[r] = fmin(lo[r], q);
+                hi[r] = fmax(hi[r], q);
+            }
+        }
+        int e[3] = {0, 0, 0}, i0[3] = {0, 0, 0};
+        if (ok) {
+            for (int r = 0; r < 3; ++r) {
+                double l = ceil((lo[r] - reach) / a.dx), h = floor((hi[r] + reach) / a.dx);
+                l = fmax(l, 0.0);
+                h = fmin(h, (double)(a.n - 1));
+                i0[r] = (int)l;
+                e[r] = h >= l ? (int)(h - l) + 1 : 0;
+            }
+        } else {
+            m.cnt[4] = 1;
+        }
+        int* b = m.box + 8 * t;
+        b[0] = i0[0]; b[1] = i0[1]; b[2] = i0[2];
+        b[3] = e[0]; b[4] = e[1]; b[5] = e[2];
+        local += (unsigned long long)e[0] * e[1] * e[2];
+    }
+    part[threadIdx.x] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) { const unsigned long long v = part[i]; part[i] = run; run += v; }
+        m.cnt[2] = run;
+        m.pre[nt] = run;
+    }
+    __syncthreads();
+    unsigned long long run = part[threadIdx.x];
+    for (int t = t0; t < t1; ++t) {
+        m.pre[t] = run;
+        const int* b = m.box + 8 * t;
+        run += (unsigned long long)b[3] * b[4] * b[5];
+    }
+}
+
+__device__ __forceinline__ int find_tri(const unsigned long long* pre, int nt, unsigned long long w) {
+    int lo = 0, hi = nt;  // pre[lo] <= w < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= w) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ bool pair_dist(const MaskWs& m, const MaskArgs& a, int t, unsigned long long local,
+                                          uint32_t* pt, T* dist) {
+    const int* b = m.box + 8 * t;
+    const unsigned long long ek = b[5], ej = b[4];
+    const int k = b[2] + (int)(local % ek);
+    const int j = b[1] + (int)((local / ek) % ej);
+    const int i = b[0] + (int)(local / (ek * ej));
+    const double px = i * a.dx, py = j * a.dx, pz = k * a.dx;
+    const int ia = a.tri[3 * t], ib = a.tri[3 * t + 1], ic = a.tri[3 * t + 2];
+    // relative to vertex a in double, then the context precision
+    const double ax = m.xg[3 * ia], ay = m.xg[3 * ia + 1], az = m.xg[3 * ia + 2];
+    T P[3] = {(T)(px - ax), (T)(py - ay), (T)(pz - az)};
+    T A0[3] = {(T)0, (T)0, (T)0};
+    T B0[3] = {(T)(m.xg[3 * ib] - ax), (T)(m.xg[3 * ib + 1] - ay), (T)(m.xg[3 * ib + 2] - az)};
+    T C0[3] = {(T)(m.xg[3 * ic] - ax), (T)(m.xg[3 * ic + 1] - ay), (T)(m.xg[3 * ic + 2] - az)};
+    T bary[3];
+    const T d = sqrt(closest_tri<T>(P, A0, B0, C0, bary));
+    *pt = (uint32_t)(((size_t)i * a.n + j) * a.n + k);
+    *dist = d;
+    return d < (T)(a.tw + a.h);
+}
+
+template <typename T>
+__global__ void k_mask_scatter1(MaskWs m, MaskArgs a, int par) {
+    const unsigned long long W = m.cnt[2];
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < W;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const int t = find_tri(m.pre, a.n_tri, w);
+        uint32_t p;
+        T d;
+        if (!pair_dist<T>(m, a, t, w - m.pre[t], &p, &d)) continue;
+        const unsigned long long old = atomicMin(&m.key[p], KeyBits<T>::of(d));
+        if (old == ~0ull) {
+            const unsigned long long slot = atomicAdd(&m.cnt[par], 1ull);
+            m.list[par][slot] = p;
+        }
+    }
+}
+
+// Pairs within a few units in the last place of the minimum (the same
+// distance recomputed here may round differently from the first pass):
+// smallest triangle index wins, so near-exact ties go to the smaller index.
+template <typename T> struct Ulps;
+template <> struct Ulps<float> {
+    static __device__ __forceinline__ float of(float d) { return d * 4.8e-7f + 1e-30f; }
+};
+template <> struct Ulps<double> {
+    static __device__ __forceinline__ double of(double d) { return d * 9.0e-16 + 1e-300; }
+};
+
+template <typename T>
+__global__ void k_mask_scatter2(MaskWs m, MaskArgs a) {
+    const unsigned long long W = m.cnt[2];
+    for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < W;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        const int t = find_tri(m.pre, a.n_tri, w);
+        uint32_t p;
+        T d;
+        if (!pair_dist<T>(m, a, t, w - m.pre[t], &p, &d)) continue;
+        const T dmin = KeyBits<T>::val(m.key[p]);
+        if (d <= dmin + Ulps<T>::of(dmin)) atomicMin(&m.win[p], t);
+    }
+}
+
+__device__ __forceinline__ double chi_profile(double d, double tw, double h, int profile) {
+    if (profile == 1) return 0.5 * (1.0 - tanh((d - tw) / h));
+    if (d <= tw - h) return 1.0;
+    if (d >= tw + h) return 0.0;
+    return 0.5 * (1.0 + cos(M_PI * (d - tw + h) / (2.0 * h)));
+}
+
+// chi and u_s at grid point p from triangle t (double throughout).
+template <typename T>
+__device__ __forceinline__ void eval_point(const MaskWs& m, const MaskArgs& a, uint32_t p, int t, T* chi, T* us,
+                                           uint8_t* flag) {
+    const size_t n = a.n, n3 = n * n * n;
+    const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+    const double X[3] = {i * a.dx, j * a.dx, k * a.dx};
+    const int id[3] = {a.tri[3 * t], a.tri[3 * t + 1], a.tri[3 * t + 2]};
+    double P[3], V[3][3];
+    for (int v = 0; v < 3; ++v)
+        for (int r = 0; r < 3; ++r) V[v][r] = m.xg[3 * id[v] + r] - m.xg[3 * id[0] + r];
+    for (int r = 0; r < 3; ++r) P[r] = X[r] - m.xg[3 * id[0] + r];
+    double bary[3];
+    const double d = sqrt(closest_tri<double>(P, V[0], V[1], V[2], bary));
+    const double c = chi_profile(d, a.tw, a.h, a.profile);
+    chi[p] = (T)c;
+    if (c > 0.0 || a.profile == 1) {
+        double vl[3] = {0, 0, 0};
+        for (int v = 0; v < 3; ++v)
+            for (int r = 0; r < 3; ++r) vl[r] += bary[v] * a.vw[3 * id[v] + r];
+        double rr[3];
+        for (int r = 0; r < 3; ++r) rr[r] = X[r] - a.XO[r];
+        const double rot[3] = {a.Om[1] * rr[2] - a.Om[2] * rr[1], a.Om[2] * rr[0] - a.Om[0] * rr[2],
+                               a.Om[0] * rr[1] - a.Om[1] * rr[0]};
+        for (int r = 0; r < 3; ++r) {
+            double g = a.VO[r] + rot[r];
+            for (int cc = 0; cc < 3; ++cc) g += a.R[3 * r + cc] * vl[cc];
+            us[r * n3 + p] = (T)g;
+        }
+        if (c > 0.0) flag[(size_t)i * n + j] = 1;
+    }
+}
+
+template <typename T>
+__global__ void k_mask_eval(MaskWs m, MaskArgs a, int par, T* chi, T* us, uint8_t* flag) {
+    const unsigned long long cnt = m.cnt[par];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = m.list[par][i];
+        const int t = m.win[p];
+        if (t >= 0 && t < a.n_tri) eval_point<T>(m, a, p, t, chi, us, flag);
+    }
+}
+
+// Dense (tanh) profile: every point against every triangle in index order.
+template <typename T>
+__global__ void k_mask_dense(MaskWs m, MaskArgs a, T* chi, T* us, uint8_t* flag) {
+    const size_t n = a.n, n3 = n * n * n;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+        T best = (T)3.0e38;
+        int bt = 0;
+        for (int t = 0; t < a.n_tri; ++t) {
+            const int ia = a.tri[3 * t], ib = a.tri[3 * t + 1], ic = a.tri[3 * t + 2];
+            if (ia < 0 || ib < 0 || ic < 0 || ia >= a.n_nodes || ib >= a.n_nodes || ic >= a.n_nodes) {
+                if (p == 0) m.cnt[4] = 1;
+                continue;
+            }
+            const double ax = m.xg[3 * ia], ay = m.xg[3 * ia + 1], az = m.xg[3 * ia + 2];
+            T P[3] = {(T)(i * a.dx - ax), (T)(j * a.dx - ay), (T)(k * a.dx - az)};
+            T A0[3] = {(T)0, (T)0, (T)0};
+            T B0[3] = {(T)(m.xg[3 * ib] - ax), (T)(m.xg[3 * ib + 1] - ay), (T)(m.xg[3 * ib + 2] - az)};
+            T C0[3] = {(T)(m.xg[3 * ic] - ax), (T)(m.xg[3 * ic + 1] - ay), (T)(m.xg[3 * ic + 2] - az)};
+            T bary[3];
+            const T d = sqrt(closest_tri<T>(P, A0, B0, C0, bary));
+            if (d < best) { best = d; bt = t; }
+        }
+        eval_point<T>(m, a, (uint32_t)p, bt, chi, us, flag);
+    }
+}
+
+// Host driver (in ps_api.cu). `par` is the index of the touched list the
+// previous call filled; the call clears those points, fills the other list
+// and returns its index in *par_out. `init` resets every key (first call);
+// `dense_dirty` zeroes chi/u_s everywhere first (after a dense mask).
+template <typename T>
+cudaError_t rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag, unsigned char* ws, int par, bool init,
+                      bool dense_dirty, cudaStream_t s, int* par_out);
+
+}  // namespace ps

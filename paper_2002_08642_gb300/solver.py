@@ -1,0 +1,127 @@
+"""Python face of libps: a Solver owning one context, its workspace tensor
+and its stream. Tensors are checked and their device pointers handed to the
+C ABI; nothing is computed here.
+"""
+import math
+
+import torch
+
+from . import binding as B
+
+_PREC = {"fp32": B.PS_FP32, "fp64": B.PS_FP64}
+_PROFILE = {"cos": B.PS_MASK_COS, "tanh": B.PS_MASK_TANH}
+_MEAN = {"fixed": B.PS_MEAN_FIXED, "free": B.PS_MEAN_FREE}
+
+
+def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
+                tw=None, h=None, x0=None):
+    dx = L / n
+    p = B.PsParams()
+    p.n = int(n)
+    p.precision = _PREC[precision]
+    p.mask_profile = _PROFILE[mask_profile]
+    p.mean_mode = _MEAN[mean_mode]
+    p.L, p.nu, p.eta, p.dt = float(L), float(nu), float(eta), float(dt)
+    p.tw = float(2.0 * dx if tw is None else tw)
+    p.h = float(1.5 * dx if h is None else h)
+    x0 = (0.5 * L, 0.5 * L, 0.5 * L) if x0 is None else x0
+    for i in range(3):
+        p.x0[i] = float(x0[i])
+    return p
+
+
+class Solver:
+    """One penalized pseudo-spectral solver on one CUDA device."""
+
+    def __init__(self, n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
+                 tw=None, h=None, x0=None, device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libps needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0)
+        self.n = int(n)
+        self.L = float(L)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.precision = precision
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            nbytes = B.ps_workspace_size(self.params)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = B.ps_init(self.params, self.stream.cuda_stream, self.workspace.data_ptr(), nbytes)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.ps_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- checks
+    def _field(self, t, comps, name):
+        n = self.n
+        shape = (comps, n, n, n) if comps > 1 else (n, n, n)
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype:
+            raise ValueError("%s must be a %s tensor on %s" % (name, self.dtype, self.device))
+        if tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError("%s must be contiguous with shape %s" % (name, shape))
+        return t.data_ptr()
+
+    # ---------------------------------------------------------------- API
+    def set_velocity(self, u):
+        B.ps_set_velocity(self.ctx, self._field(u, 3, "u"))
+
+    def velocity(self, out=None):
+        n = self.n
+        if out is None:
+            out = torch.empty((3, n, n, n), dtype=self.dtype, device=self.device)
+        B.ps_get_velocity(self.ctx, self._field(out, 3, "out"))
+        return out
+
+    def set_mask(self, chi, us):
+        B.ps_set_mask(self.ctx, self._field(chi, 1, "chi"), self._field(us, 3, "us"))
+
+    def mask(self):
+        n = self.n
+        chi = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
+        us = torch.empty((3, n, n, n), dtype=self.dtype, device=self.device)
+        B.ps_get_mask(self.ctx, chi.data_ptr(), us.data_ptr())
+        return chi, us
+
+    def set_mask_from_nodes(self, xw, vw, tri, frame):
+        for t, nm, dt in ((xw, "xw", torch.float64), (vw, "vw", torch.float64), (tri, "tri", torch.int32)):
+            if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous %s tensor on %s" % (nm, dt, self.device))
+            if t.dim() != 2 or t.shape[1] != 3:
+                raise ValueError("%s must have shape (k, 3)" % nm)
+        if xw.shape != vw.shape:
+            raise ValueError("xw and vw must have the same shape")
+        B.ps_set_mask_from_nodes(self.ctx, xw.data_ptr(), vw.data_ptr(), xw.shape[0], tri.data_ptr(),
+                                 tri.shape[0], B.make_frame(frame))
+
+    def step(self, nsteps=1):
+        B.ps_step(self.ctx, int(nsteps))
+
+    def forces(self):
+        return B.ps_forces(self.ctx)
+
+    def diagnostics(self):
+        return B.ps_diagnostics(self.ctx)
+
+    def timing(self, on=True):
+        B.ps_timing_enable(self.ctx, on)
+
+    def timing_read(self):
+        return B.ps_timing_read(self.ctx)
+
+    def state_buffer(self):
+        return torch.empty(B.ps_state_size(self.ctx), dtype=torch.uint8, device=self.device)
+
+    def save_state(self, buf):
+        B.ps_save_state(self.ctx, buf.data_ptr())
+
+    def restore_state(self, buf):
+        B.ps_restore_state(self.ctx, buf.data_ptr())
