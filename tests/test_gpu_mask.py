@@ -43,6 +43,7 @@ def test_rasterise_matches_oracle(n, nodes, prec):
     dx = L / n
     g = Solver(n, L, 1e-3, 1e-3, 5e-4, precision=prec)
     tolc = 1e-12 if prec == "fp64" else 2e-6
+    tolu = 1e-12 if prec == "fp64" else 1e-6   # u_s is stored in the context precision
     # two calls: the second must clear the first call's band
     for t in (0.37, 0.5):
         xw, vw, tri, fr = wing(t, nodes)
@@ -53,7 +54,7 @@ def test_rasterise_matches_oracle(n, nodes, prec):
         assert band.sum() > 100
         # u_s is continuous across shared edges, so argmin ties agree closely
         du = np.abs(us - us_o).max(axis=0)
-        frac = np.mean(du[band] > 1e-9)
+        frac = np.mean(du[band] > tolu)
         assert frac < 1e-3, frac
         assert du.max() < 1e-3
         assert np.all(us[:, ~(band | (chi > 0))] == 0)
