@@ -52,10 +52,18 @@ def test_rasterise_matches_oracle(n, nodes, prec):
         assert np.max(np.abs(chi - chi_o)) < tolc
         band = chi_o > 0
         assert band.sum() > 100
-        # u_s is continuous across shared edges, so argmin ties agree closely
+        # u_s must match wherever the closest triangle is unambiguous at the
+        # precision the argmin is taken in (relative gap to the runner-up
+        # above 1e-5); at near-ties a different but equally close triangle
+        # may win and u_s then differs by the barycentric blend only.
         du = np.abs(us - us_o).max(axis=0)
-        frac = np.mean(du[band] > tolu)
-        assert frac < 1e-3, frac
+        xg = OM.global_nodes(xw, fr)
+        P = np.stack(inputs.grid(n, L), axis=-1)[band]
+        D = np.stack([OM.closest_point_on_triangle(P, *xg[t])[0] for t in tri], axis=1)
+        D.sort(axis=1)
+        clear = (D[:, 1] - D[:, 0]) > 1e-5 * np.maximum(D[:, 0], dx)
+        assert clear.mean() > 0.5
+        assert np.max(du[band][clear]) < tolu
         assert du.max() < 1e-3
         assert np.all(us[:, ~(band | (chi > 0))] == 0)
 
