@@ -168,6 +168,29 @@ ps_status ps_timing_enable(ps_ctx* ctx, int32_t on);
 ps_status ps_timing_read(ps_ctx* ctx, double* ms, int64_t* launches, int32_t cap, int32_t* count);
 const char* ps_timing_name(int32_t i);
 
+/* Penalization force and moment of caller-supplied physical fields, for
+ * callers that cannot allocate device memory (code inside someone else's
+ * CUDA-graph capture, host callbacks, allocation-free real-time loops): it
+ * needs no ps_ctx and no workspace. The paper has no counterpart; it is the
+ * force reduction of ps_step (F = (dx^3/eta) sum chi (u - u_s),
+ * M = (dx^3/eta) sum (x - x0) x chi (u - u_s), x = (i, j, k) dx) offered alone.
+ *   n, precision, L, eta, x0  grid size, PS_FP32/PS_FP64 (type of the real
+ *              arrays), box length, penalization constant, moment point
+ *              (host array of 3 doubles)
+ *   u_dev (3*n^3), chi_dev (n^3), us_dev (3*n^3)  physical fields, layout as
+ *              everywhere in this header
+ *   FM_dev     device output, 6 doubles: F then M
+ *   cuda_stream  stream the work is enqueued on (asynchronous)
+ * Scratch lives in a fixed 48 KiB array compiled into the library (one
+ * partial per x-plane, 1024 planes): n > 1024 returns PS_EINVAL. Nothing is
+ * allocated: no cudaMalloc, no cudaFree. The first call on each device looks
+ * up the array's device address; make it before any stream capture. Calls
+ * share the array: two calls that may overlap on the GPU (unordered streams)
+ * race. Returns PS_ECUDA if a launch fails. */
+ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision, double L, double eta,
+                                        const double x0[3], const void* u_dev, const void* chi_dev,
+                                        const void* us_dev, double* FM_dev, void* cuda_stream);
+
 /* Text of the last error on this context ("" if none). */
 const char* ps_last_error(const ps_ctx* ctx);
 

@@ -60,6 +60,8 @@ _SIGS = {
     "ps_timing_read": (c_int32, [c_void_p, _P(c_double), _P(ctypes.c_int64), c_int32, _P(c_int32)]),
     "ps_timing_name": (ctypes.c_char_p, [c_int32]),
     "ps_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ps_penalization_force_noalloc": (c_int32, [c_int32, c_int32, c_double, c_double, _P(c_double), c_void_p,
+                                                c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -200,6 +202,14 @@ def ps_timing_read(ctx):
 def ps_last_error(ctx):
     raw = lib().ps_last_error(ctx)
     return raw.decode() if raw else ""
+
+
+def ps_penalization_force_noalloc(n, precision, L, eta, x0, u_ptr, chi_ptr, us_ptr, fm_ptr, stream_ptr):
+    """Allocation-free force/moment of caller fields into fm (6 device doubles)."""
+    x = (c_double * 3)(*[float(v) for v in x0])
+    check(lib().ps_penalization_force_noalloc(int(n), int(precision), float(L), float(eta), x, c_void_p(u_ptr),
+                                              c_void_p(chi_ptr), c_void_p(us_ptr), c_void_p(fm_ptr),
+                                              c_void_p(stream_ptr)))
 
 
 def make_frame(fr):
