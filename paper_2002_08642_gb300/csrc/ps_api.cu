@@ -23,6 +23,7 @@ struct ps_ctx {
     int device;
     int fp64;
     const Ops* ops;
+    int zblocks;        // force partials written by the z pass
     KP kp;
     Bufs b;
     size_t elem;        // bytes of one real
@@ -54,7 +55,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int tile_width(int fp64) { return fp64 ? 8 : 16; }
 
 struct Layout {
-    size_t U, H, A, B, chi, us, flag, tw, Ex, Ez, partial, out, mask, total;
+    size_t U, H, A, B, chi, us, flag, tw, Ex, Ez, partial, out, err, mask, total;
     size_t ustate, mask_bytes;
 };
 
@@ -81,9 +82,10 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->tw = take((size_t)n * ec);
     L->Ex = take((size_t)K * er);
     L->Ez = take((size_t)Kz * er);
-    const size_t nparts = (size_t)(ops ? ops->zblocks : n * n) + 4096;
+    const size_t nparts = (size_t)n * n + 4096;
     L->partial = take(nparts * 6 * sizeof(double));
     L->out = take(64 * sizeof(double));
+    L->err = take(256);
     L->mask_bytes = mask_workspace_bytes(n);
     L->mask = take(L->mask_bytes);
     L->total = off;
@@ -386,10 +388,14 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     c->b.Ez = w + L.Ez;
     c->b.partial = (double*)(w + L.partial);
     c->out = (double*)(w + L.out);
+    c->b.err = (int*)(w + L.err);
     c->mask_ws = w + L.mask;
     c->mask_ws_bytes = L.mask_bytes;
 
-    cudaError_t e = ops->prepare();
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (nsm < 1) nsm = 1;
+    cudaError_t e = ops->prepare(nsm, &c->zblocks);
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;
     if (c->fp64) host_tables<double>(p, tw, ex, ez);
@@ -528,14 +534,17 @@ ps_status ps_forces(ps_ctx* c, double F[3], double M[3]) {
     if (c->nstep == 0) return fail(c, PS_ESTATE, "ps_forces: no step taken yet");
     DeviceGuard dg(c->device);
     const double dx = c->kp.dx;
-    k_force_final<<<1, 256, 0, c->stream>>>(c->b.partial, c->ops->zblocks, dx * dx * dx / c->p.eta, c->out);
+    k_force_final<<<1, 256, 0, c->stream>>>(c->b.partial, c->zblocks, dx * dx * dx / c->p.eta, c->out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "ps_forces");
     double h[6];
-    if ((e = cudaMemcpyAsync(h, c->out, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    int derr = 0;
+    if ((e = cudaMemcpyAsync(h, c->out, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&derr, c->b.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ps_forces copy");
     ps_status s = sync(c, "ps_forces");
     if (s != PS_OK) return s;
+    if (derr) return fail(c, PS_ECUDA, "a device-side copy wait gave up (results of the affected steps are invalid)");
     for (int i = 0; i < 3; ++i) { F[i] = h[i]; M[i] = h[3 + i]; }
     return PS_OK;
 }

@@ -18,12 +18,13 @@ struct Bufs {
     void* Ex;        // exp(-nu kx^2 dt) for the K x/y modes (T)
     void* Ez;        // exp(-nu kz^2 dt) for the Kz z modes (T)
     double* partial; // per-block partial sums
+    int* err;        // device error flag (bounded waits that gave up)
 };
 
 struct Ops {
     int n, C, C5, LY, G;
-    int zblocks;  // blocks of the z pass (= number of force partials)
-    cudaError_t (*prepare)();
+    int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
+    cudaError_t (*prepare)(int nsm, int* zblocks);
     // ev (nullable): 6 events recorded before pass 1 and after each pass
     cudaError_t (*step)(const KP&, const Bufs&, int first, cudaStream_t, cudaEvent_t* ev);
     cudaError_t (*set_velocity)(const KP&, const Bufs&, const void* u, cudaStream_t);
@@ -37,32 +38,46 @@ template <typename T, int N> struct Engine {
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
     static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2);
+    static constexpr size_t sm_zp = (size_t)GE::zsmem(GE::LZ);
     static constexpr int thr_s = GE::C * GE::G;
     static constexpr int thr_5 = GE::C5 * GE::G;
     static constexpr int thr_z = GE::LY * GE::G;
+    static constexpr int thr_zp = 3 * GE::LZ * GE::G;
 
     template <class K> static cudaError_t attr(K k, size_t bytes) {
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     }
 
-    static cudaError_t prepare() {
+    static int& zgrid() {  // persistent z-pass blocks (set by prepare)
+        static int g = 0;
+        return g;
+    }
+
+    static cudaError_t prepare(int nsm, int* zb) {
         cudaError_t e;
         if ((e = attr(k_xinv<T, N, 6>, sm_strided))) return e;
         if ((e = attr(k_xinv<T, N, 3>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 6>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 3>, sm_strided))) return e;
         if ((e = attr(k_yfwd<T, N>, sm_strided))) return e;
-        if ((e = attr(k_zpass<T, N>, sm_z))) return e;
+        if ((e = attr(k_zpass<T, N>, sm_zp))) return e;
         if ((e = attr(k_zfwd_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
+        int occ = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, N>, thr_zp, sm_zp))) return e;
+        if (occ < 1) occ = 1;
+        const int nb = N * N / GE::LZ;
+        zgrid() = nsm * occ < nb ? nsm * occ : nb;
+        *zb = zgrid();
         return cudaSuccess;
     }
 
     static dim3 grid_xs(const KP& kp, int C) { return dim3(kp.Kzp / C, kp.K); }
     static dim3 grid_ys(const KP& kp) { return dim3(kp.Kzp / GE::C, N); }
     static int zblocks() { return N * N / GE::LY; }
+
 
     static cudaError_t step(const KP& kp, const Bufs& b, int first, cudaStream_t s, cudaEvent_t* ev) {
         const C2* tw = (const C2*)b.tw;
@@ -71,8 +86,8 @@ template <typename T, int N> struct Engine {
         if (ev) cudaEventRecord(ev[1], s);
         k_yinv<T, N, 6><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
         if (ev) cudaEventRecord(ev[2], s);
-        k_zpass<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                     b.flag, b.partial, tw);
+        k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+                                                   b.flag, b.partial, tw, b.err);
         if (ev) cudaEventRecord(ev[3], s);
         k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
         if (ev) cudaEventRecord(ev[4], s);
@@ -102,7 +117,7 @@ template <typename T, int N> struct Engine {
     static Ops ops() {
         Ops o;
         o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
-        o.zblocks = zblocks();
+        o.zblocks = 0;
         o.prepare = &prepare;
         o.step = &step;
         o.set_velocity = &set_velocity;

@@ -196,7 +196,7 @@ template <typename T, int N, int SIGN> struct LineFFT {
 
     template <int s, bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
-                                                 const Load& load, const Store& store) {
+                                                 const Load& load, const Store& store, bool on = true) {
         constexpr int r = radix_at(N, s);
         constexpr int Ls = ls_at(N, s);
         constexpr int NBF = N / r;
@@ -204,51 +204,75 @@ template <typename T, int N, int SIGN> struct LineFFT {
         constexpr bool last = (s == S - 1);
         constexpr bool from_tile = (s > 0) || FROM_TILE;
         constexpr int two = tw_offset(N, s);
-        C v[NB][r];
+        // one butterfly: inputs, twiddles, DFT
+        auto gather = [&](int j, C* v) {
+            const int k = j % Ls;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const int j = g + b * G;
-            if (NB * G == NBF || j < NBF) {
-                const int k = j % Ls;
-#pragma unroll
-                for (int t = 0; t < r; ++t) {
-                    C x;
-                    if constexpr (from_tile) x = tile[addr(j + t * NBF)];
-                    else x = load(j + t * NBF);
-                    if constexpr (Ls > 1) {
-                        if (t > 0) {
-                            C w = tw[two + (t - 1) * Ls + k];
-                            if constexpr (SIGN < 0) w.y = -w.y;
-                            x = cmul(x, w);
-                        }
+            for (int t = 0; t < r; ++t) {
+                C x;
+                if constexpr (from_tile) x = tile[addr(j + t * NBF)];
+                else x = load(j + t * NBF);
+                if constexpr (Ls > 1) {
+                    if (t > 0) {
+                        C w = tw[two + (t - 1) * Ls + k];
+                        if constexpr (SIGN < 0) w.y = -w.y;
+                        x = cmul(x, w);
                     }
-                    v[b][t] = x;
                 }
+                v[t] = x;
             }
-        }
-        if constexpr (from_tile && !last) __syncthreads();
+        };
+        auto scatter = [&](int j, C* v) {
+            const int k = j % Ls;
+            Dft<r, SIGN, C>::run(v);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const int j = g + b * G;
-            if (NB * G == NBF || j < NBF) {
-                const int k = j % Ls;
-                Dft<r, SIGN, C>::run(v[b]);
+            for (int u = 0; u < r; ++u) {
+                const int o = (j - k) * r + k + u * Ls;
+                if constexpr (last) store(o, v[u]);
+                else tile[addr(o)] = v[u];
+            }
+        };
+        if constexpr (from_tile && !last) {
+            // in place: every read of the stage before any write
+            C v[NB][r];
 #pragma unroll
-                for (int u = 0; u < r; ++u) {
-                    const int o = (j - k) * r + k + u * Ls;
-                    if constexpr (last) store(o, v[b][u]);
-                    else tile[addr(o)] = v[b][u];
+            for (int b = 0; b < NB; ++b) {
+                const int j = g + b * G;
+                if (on && (NB * G == NBF || j < NBF)) gather(j, v[b]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int j = g + b * G;
+                if (on && (NB * G == NBF || j < NBF)) scatter(j, v[b]);
+            }
+        } else {
+            // reads from the functor, or the last stage (each butterfly reads
+            // and writes the same positions): one butterfly at a time
+#pragma unroll 1
+            for (int b = 0; b < NB; ++b) {
+                const int j = g + b * G;
+                if (on && (NB * G == NBF || j < NBF)) {
+                    C v[r];
+                    gather(j, v);
+                    scatter(j, v);
                 }
             }
         }
         if constexpr (!last) __syncthreads();
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE>(tile, tw, addr, g, load, store);
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE>(tile, tw, addr, g, load, store, on);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run(C* tile, const C* tw, const Addr& addr, int g,
                                                const Load& load, const Store& store) {
-        stage<0, FROM_TILE>(tile, tw, addr, g, load, store);
+        stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true);
+    }
+    // Same, but threads with on == false only take part in the barriers.
+    template <bool FROM_TILE, class Addr, class Load, class Store>
+    static __device__ __forceinline__ void run_masked(C* tile, const C* tw, const Addr& addr, int g,
+                                                      const Load& load, const Store& store, bool on) {
+        stage<0, FROM_TILE>(tile, tw, addr, g, load, store, on);
     }
 };
 

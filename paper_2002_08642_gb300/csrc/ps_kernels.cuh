@@ -25,6 +25,7 @@
 //   5 x-forward truncated to K rows, 1/n^3, P, integrating-factor
 //     AB2 (Euler on the first step)                                  A,U,H -> U,H
 #pragma once
+#include "ps_async.cuh"
 #include "ps_fft.cuh"
 
 namespace ps {
@@ -95,6 +96,20 @@ template <typename T, int N> struct Geo {
     static constexpr int LYa = ly_threads() < ly_smem() ? ly_threads() : ly_smem();
     static constexpr int ly_fix(int l) { while (l > 1 && (N * N) % l != 0) l /= 2; return l; }
     static constexpr int LY = ly_fix(LYa);
+    // kept z modes, padded to the tile width
+    static constexpr int KZ = (N - 1) / 3 + 1;
+    static constexpr int KZP = (KZ + CW - 1) / CW * CW;
+    // z pass: LZ lines per batch (even, divides n^2), 3 LZ G threads, two
+    // staging buffers of the batch's six spectral lines plus the FFT tiles
+    static constexpr int zsmem(int l) {
+        return (int)sizeof(C2) * (2 * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1);
+    }
+    static constexpr int lz_pick() {
+        int l = 2;
+        while (3 * (2 * l) * G <= 768 && zsmem(2 * l) <= 200 * 1024 && (N * N) % (2 * l) == 0) l *= 2;
+        return l;
+    }
+    static constexpr int LZ = lz_pick();
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
 
@@ -190,115 +205,196 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 }
 
 // ---------------------------------------------------------------- pass 3
-// z lines of (x, y): c2r of six fields as three complex lines
-// (u_x + i u_y, u_z + i w_x, w_y + i w_z), the pointwise nonlinear and
-// penalization term, force/moment partials, r2c of n as (n_x + i n_y) and
-// (n_z + 0 i), truncated to kz < Kz, written over fields 0..2 of B.
+// z lines of (x, y), in batches of LZ consecutive lines, persistent blocks.
+// The six spectral lines of the next batch are fetched by bulk asynchronous
+// copies into the other staging buffer while the current batch is computed.
+// Per line: three complex inverse transforms (u_x + i u_y, u_z + i w_x,
+// w_y + i w_z) run side by side by three thread groups; n = u x omega -
+// (chi/eta)(u - u_s) pointwise with the force/moment partial sums in double;
+// forward transforms of (n_x + i n_y) per line and of (n_z[l] + i n_z[l+1])
+// per line pair; the result, truncated to kz < Kz, overwrites fields 0..2 of
+// B (only this batch's lines, whose input is already in shared memory).
 template <typename T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
+__global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, 1)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
-        const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg) {
+        const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
+        int* __restrict__ err) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
-    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
+    constexpr int nbatch = N * N / LZ;
+    constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* tiles = tw + GE::tw_n;
-    __shared__ double red[32 * 6];
-    const int line = threadIdx.x / G, g = threadIdx.x % G;
-    const long lid = (long)blockIdx.x * LY + line;
-    const int x = (int)(lid / N), y = (int)(lid % N);
-    const int Kz = kp.Kz, Kzp = kp.Kzp;
-    const size_t BS = (size_t)N * N * Kzp;
-    const size_t lo = ((size_t)x * N + y) * Kzp;
-    load_tw(tw, twg, GE::tw_n);
-    auto addr = [&](int p) { return zaddr(p, line, LP); };
-    C2* t0 = tiles;
-    C2* t1 = tiles + LY * LP;
-    C2* t2 = tiles + 2 * LY * LP;
-    __syncthreads();
-#pragma unroll 1
-    for (int pr = 0; pr < 3; ++pr) {
-        C2* tp = tiles + pr * LY * LP;
-        const C2* fa = B + (2 * pr) * BS + lo;
-        const C2* fb = B + (2 * pr + 1) * BS + lo;
-        auto load = [&](int q) -> C2 {
-            if (q < Kz) {
-                C2 a = fa[q], b = fb[q];
-                if (q == 0) { a.y = 0; b.y = 0; }
-                return cmk<C2>(a.x - b.y, a.y + b.x);          // A + i B
-            }
-            if (q > N - Kz) {
-                C2 a = fa[N - q], b = fb[N - q];
-                return cmk<C2>(a.x + b.y, b.x - a.y);          // conj(A) + i conj(B)
-            }
-            return cmk<C2>((T)0, (T)0);
-        };
-        auto store = [&](int p, C2 v) { tp[addr(p)] = v; };
-        LineFFT<T, N, 1>::template run<false>(tp, tw, addr, g, load, store);
+    C2* stage = reinterpret_cast<C2*>(smraw);           // [2][6][LZ][KZP]
+    C2* tiles = stage + 2 * 6 * LZ * KZP;                // [LZ][3][LP]
+    C2* tw = tiles + 3 * LZ * LP;
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double wacc[32][12];     // per-warp (sum, compensation) of the six sums
+    const int fl = threadIdx.x / G, g = threadIdx.x % G;
+    const int pl = fl / 3, pr = fl % 3;
+    const int Kz = kp.Kz;
+    const size_t BS = (size_t)N * N * KZP;
+    auto tile = [&](int l, int p) { return tiles + (size_t)(l * 3 + p) * LP; };
+    auto zad = [](int p) { return p + (p >> 4); };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
     }
+    load_tw(tw, twg, GE::tw_n);
+    for (int i = threadIdx.x; i < 32 * 12; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
     __syncthreads();
-    // pointwise: n = u x w - (chi/eta)(u - us); forces in double
-    double fm[6] = {0, 0, 0, 0, 0, 0};
-    const bool has_mask = flag[(size_t)x * N + y] != 0;
-    const size_t po = ((size_t)x * N + y) * N;
+    auto issue = [&](int b, int buf) {  // one thread
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], 6 * fbytes);
+        // kept rolled: fully unrolled, the six copies crashed ptxas 13.0 at n = 768
+#pragma unroll 1
+        for (int f = 0; f < 6; ++f)
+            bulk_g2s(stage + (size_t)(buf * 6 + f) * LZ * KZP, B + f * BS + (size_t)b * LZ * KZP, fbytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < nbatch) issue(blockIdx.x, 0);
+
     const size_t N3 = (size_t)N * N * N;
     const T inv_eta = (T)kp.inv_eta;
-    Acc acc[6] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int z = g; z < N; z += G) {
-        const int a = addr(z);
-        C2 z0 = t0[a], z1 = t1[a], z2 = t2[a];
-        const T ux = z0.x, uy = z0.y, uz = z1.x, wx = z1.y, wy = z2.x, wz = z2.y;
-        T nx = uy * wz - uz * wy;
-        T ny = uz * wx - ux * wz;
-        T nz = ux * wy - uy * wx;
-        if (has_mask) {
-            const T c = chi[po + z];
-            if (c != (T)0) {
-                const T sx = us[po + z], sy = us[N3 + po + z], sz = us[2 * N3 + po + z];
-                const T ce = c * inv_eta;
-                nx -= ce * (ux - sx);
-                ny -= ce * (uy - sy);
-                nz -= ce * (uz - sz);
-                const double cd = (double)c;
-                const double px = cd * ((double)ux - (double)sx);
-                const double py = cd * ((double)uy - (double)sy);
-                const double pz = cd * ((double)uz - (double)sz);
-                const double rx = x * kp.dx - kp.x0[0], ry = y * kp.dx - kp.x0[1], rz = z * kp.dx - kp.x0[2];
-                acc[0].add(px);
-                acc[1].add(py);
-                acc[2].add(pz);
-                acc[3].add(ry * pz - rz * py);
-                acc[4].add(rz * px - rx * pz);
-                acc[5].add(rx * py - ry * px);
+    int it = 0;
+    for (int b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = b + (int)gridDim.x < nbatch;
+        if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: record it, let any other copy land, stop
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const C2* st = stage + (size_t)buf * 6 * LZ * KZP;
+        // spectral lines -> two-for-one complex lines in the tiles
+        for (int idx = threadIdx.x; idx < 3 * LZ * N; idx += blockDim.x) {
+            const int q = idx % N, lp = idx / N, l = lp / 3, p = lp % 3;
+            const C2* fa = st + (size_t)((2 * p) * LZ + l) * KZP;
+            const C2* fb = st + (size_t)((2 * p + 1) * LZ + l) * KZP;
+            C2 v = cmk<C2>((T)0, (T)0);
+            if (q < Kz) {
+                C2 a = fa[q], c = fb[q];
+                if (q == 0) { a.y = 0; c.y = 0; }
+                v = cmk<C2>(a.x - c.y, a.y + c.x);                 // A + i B
+            } else if (q > N - Kz) {
+                const C2 a = fa[N - q], c = fb[N - q];
+                v = cmk<C2>(a.x + c.y, c.x - a.y);                 // conj(A) + i conj(B)
+            }
+            tile(l, p)[zad(q)] = v;
+        }
+        __syncthreads();
+        {
+            const int tbase = (int)(tile(pl, pr) - tiles);
+            auto addr = [&](int p) { return tbase + zad(p); };
+            auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
+            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
+            LineFFT<T, N, 1>::template run<true>(tiles, tw, addr, g, noload, store);
+        }
+        __syncthreads();
+        double fm[6] = {0, 0, 0, 0, 0, 0};
+        bool touched = false;
+        for (int idx = threadIdx.x; idx < LZ * N; idx += blockDim.x) {
+            const int l = idx / N, z = idx % N;
+            const long lid = (long)b * LZ + l;
+            const int a = zad(z);
+            C2* t0 = tile(l, 0);
+            C2* t1 = tile(l, 1);
+            C2* t2 = tile(l, 2);
+            const C2 z0 = t0[a], z1 = t1[a], z2 = t2[a];
+            const T ux = z0.x, uy = z0.y, uz = z1.x, wx = z1.y, wy = z2.x, wz = z2.y;
+            T nx = uy * wz - uz * wy;
+            T ny = uz * wx - ux * wz;
+            T nz = ux * wy - uy * wx;
+            if (flag[lid] != 0) {
+                const size_t po = (size_t)lid * N + z;
+                const T c = chi[po];
+                if (c != (T)0) {
+                    const int x = (int)(lid / N), y = (int)(lid % N);
+                    const T sx = us[po], sy = us[N3 + po], sz = us[2 * N3 + po];
+                    const T ce = c * inv_eta;
+                    nx -= ce * (ux - sx);
+                    ny -= ce * (uy - sy);
+                    nz -= ce * (uz - sz);
+                    const double cd = (double)c;
+                    const double px = cd * ((double)ux - (double)sx);
+                    const double py = cd * ((double)uy - (double)sy);
+                    const double pz = cd * ((double)uz - (double)sz);
+                    const double rx = x * kp.dx - kp.x0[0], ry = y * kp.dx - kp.x0[1], rz = z * kp.dx - kp.x0[2];
+                    fm[0] += px;
+                    fm[1] += py;
+                    fm[2] += pz;
+                    fm[3] += ry * pz - rz * py;
+                    fm[4] += rz * px - rx * pz;
+                    fm[5] += rx * py - ry * px;
+                    touched = true;
+                }
+            }
+            // this thread alone reads and writes these slots of line l
+            t0[a] = cmk<C2>(nx, ny);
+            reinterpret_cast<T*>(t2 + a)[0] = nz;
+        }
+        // this batch's force sums: warp tree, then compensated into the warp slot
+        if (__any_sync(0xffffffffu, touched)) {
+            for (int i = 0; i < 6; ++i)
+                for (int o = 16; o > 0; o >>= 1) fm[i] += __shfl_down_sync(0xffffffffu, fm[i], o);
+            if ((threadIdx.x & 31) == 0) {
+                double* w = wacc[threadIdx.x >> 5];
+                for (int i = 0; i < 6; ++i) {
+                    Acc a = {w[2 * i], w[2 * i + 1]};
+                    a.add(fm[i]);
+                    w[2 * i] = a.s;
+                    w[2 * i + 1] = a.c;
+                }
             }
         }
-        t0[a] = cmk<C2>(nx, ny);
-        t1[a] = cmk<C2>(nz, (T)0);
-    }
-    for (int i = 0; i < 6; ++i) fm[i] = acc[i].val();
-    __syncthreads();
-#pragma unroll 1
-    for (int pr = 0; pr < 2; ++pr) {
-        C2* tp = tiles + pr * LY * LP;
-        auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
-        auto store = [&](int p, C2 v) { tp[addr(p)] = v; };
-        LineFFT<T, N, -1>::template run<true>(tp, tw, addr, g, noload, store);
+        __syncthreads();
+        // n_z of lines 2m and 2m+1 share one complex line: (n_z[2m] + i n_z[2m+1])
+        for (int idx = threadIdx.x; idx < (LZ / 2) * N; idx += blockDim.x) {
+            const int l = 2 * (idx / N), a = zad(idx % N);
+            tile(l, 1)[a] = cmk<C2>(tile(l, 2)[a].x, tile(l + 1, 2)[a].x);
+        }
+        __syncthreads();
+        {
+            // forward lines: (l, 0) for every l, (l, 1) for even l; others idle
+            const bool active = (pr == 0) || (pr == 1 && (pl & 1) == 0);
+            const int tbase = (int)(tile(pl, pr == 2 ? 1 : pr) - tiles);
+            auto addr = [&](int p) { return tbase + zad(p); };
+            auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
+            auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
+            LineFFT<T, N, -1>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
+        }
+        __syncthreads();
+        // unpack the two-for-one transforms, keep kz < Kz
+        for (int idx = threadIdx.x; idx < LZ * Kz; idx += blockDim.x) {
+            const int l = idx / Kz, k = idx % Kz;
+            const size_t lo = ((size_t)b * LZ + l) * KZP;
+            const C2* t0 = tile(l, 0);
+            const C2* t1 = tile(l & ~1, 1);
+            const int m = (N - k) % N;
+            const C2 zk = t0[zad(k)], zm = t0[zad(m)];
+            // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
+            B[lo + k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            B[BS + lo + k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+            const C2 wk = t1[zad(k)], wm = t1[zad(m)];
+            B[2 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
+                                         : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
+        }
         __syncthreads();
     }
-    // unpack the two-for-one transform, keep kz < Kz
-    C2* o0 = B + lo;
-    C2* o1 = B + BS + lo;
-    C2* o2 = B + 2 * BS + lo;
-    for (int k = g; k < Kz; k += G) {
-        const C2 zk = t0[addr(k)];
-        const C2 zm = t0[addr((N - k) % N)];
-        // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
-        o0[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-        o1[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
-        o2[k] = t1[addr(k)];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        Acc a = {0, 0};
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+            a.add(wacc[w][2 * threadIdx.x]);
+            a.add(wacc[w][2 * threadIdx.x + 1]);
+        }
+        partial[(size_t)blockIdx.x * 6 + threadIdx.x] = a.val();
     }
-    block_sum<6>(fm, partial + (size_t)blockIdx.x * 6, red);
 }
 
 // ---------------------------------------------------------------- pass 4
