@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "ps.h"
 #include "ps_engine.cuh"
 #include "ps_mask.cuh"
@@ -34,6 +36,7 @@ struct ps_ctx {
     int mask_par;             // touched list filled by the last rasterisation
     bool mask_init;           // rasteriser keys initialised
     bool mask_dense_dirty;    // chi/u_s may be nonzero outside the touched list
+    CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
     int nstep;
     int has_velocity;
     // per-pass timing: a ring of events, kTimingRing steps deep
@@ -94,6 +97,35 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
 
 const Ops* ops_for(const ps_params* p) {
     return p->precision == PS_FP64 ? ops_f64(p->n) : ops_f32(p->n);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D map over `rows` rows of 2 Kzp reals (complex rows of Kzp), box of
+// `bc` complex columns by `br` rows.
+bool encode_rows(CUtensorMap* tm, void* base, int fp64, size_t rows, int Kzp, int bc, int br) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const size_t er = fp64 ? 8 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * Kzp), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * Kzp * er)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * bc), (cuuint32_t)br};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(tm, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 ps_status fail(ps_ctx* c, ps_status s, const std::string& msg) {
@@ -396,6 +428,16 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm < 1) nsm = 1;
     cudaError_t e = ops->prepare(nsm, &c->zblocks);
+    if (e == cudaSuccess) {
+        const int Kk = 2 * mm + 1;
+        if (!encode_rows(&c->tmA, c->b.A, c->fp64, (size_t)6 * n * Kk, kp.Kzp, ops->cy2, ops->br2) ||
+            !encode_rows(&c->tmB, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4, ops->br4)) {
+            delete c;
+            return PS_ECUDA;
+        }
+        c->b.tmA = &c->tmA;
+        c->b.tmB = &c->tmB;
+    }
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;
     if (c->fp64) host_tables<double>(p, tw, ex, ez);

@@ -19,10 +19,13 @@ struct Bufs {
     void* Ez;        // exp(-nu kz^2 dt) for the Kz z modes (T)
     double* partial; // per-block partial sums
     int* err;        // device error flag (bounded waits that gave up)
+    const CUtensorMap* tmA;  // A as rows of 2 Kzp reals (y-inverse input)
+    const CUtensorMap* tmB;  // B as rows of 2 Kzp reals (y-forward input)
 };
 
 struct Ops {
     int n, C, C5, LY, G;
+    int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
     cudaError_t (*prepare)(int nsm, int* zblocks);
     // ev (nullable): 6 events recorded before pass 1 and after each pass
@@ -52,6 +55,18 @@ template <typename T, int N> struct Engine {
         static int g = 0;
         return g;
     }
+    static int& y2grid() {
+        static int g = 0;
+        return g;
+    }
+    static int& y4grid() {
+        static int g = 0;
+        return g;
+    }
+    static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2);
+    static constexpr size_t sm_y4 = (size_t)GE::y4_smem(GE::CY4);
+    static constexpr int thr_y2 = GE::CY2 * GE::G;
+    static constexpr int thr_y4 = GE::CY4 * GE::G;
 
     static cudaError_t prepare(int nsm, int* zb) {
         cudaError_t e;
@@ -71,6 +86,12 @@ template <typename T, int N> struct Engine {
         const int nb = N * N / GE::LZ;
         zgrid() = nsm * occ < nb ? nsm * occ : nb;
         *zb = zgrid();
+        if ((e = attr(k_yinv_tma<T, N>, sm_y2))) return e;
+        if ((e = attr(k_yfwd_tma<T, N>, sm_y4))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yinv_tma<T, N>, thr_y2, sm_y2))) return e;
+        y2grid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N>, thr_y4, sm_y4))) return e;
+        y4grid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
     }
 
@@ -84,12 +105,12 @@ template <typename T, int N> struct Engine {
         if (ev) cudaEventRecord(ev[0], s);
         k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
         if (ev) cudaEventRecord(ev[1], s);
-        k_yinv<T, N, 6><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
+        k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, kp, (C2*)b.B, tw, b.err);
         if (ev) cudaEventRecord(ev[2], s);
         k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                    b.flag, b.partial, tw, b.err);
         if (ev) cudaEventRecord(ev[3], s);
-        k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
+        k_yfwd_tma<T, N><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, kp, (C2*)b.A, tw, b.err);
         if (ev) cudaEventRecord(ev[4], s);
         k_xfwd<T, N, 0><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
                                                                  (const T*)b.Ex, (const T*)b.Ez, first, tw);
@@ -117,6 +138,7 @@ template <typename T, int N> struct Engine {
     static Ops ops() {
         Ops o;
         o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
+        o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
         o.zblocks = 0;
         o.prepare = &prepare;
         o.step = &step;
@@ -126,8 +148,12 @@ template <typename T, int N> struct Engine {
     }
 };
 
-// Grid sizes built into the library.
+// Grid sizes built into the library (a tuning build may restrict them).
+#ifdef PS_TUNING_SIZES
+#define PS_SIZES(X) X(256) X(768)
+#else
 #define PS_SIZES(X) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
+#endif
 
 // Defined in the per-precision translation units.
 const Ops* ops_f32(int n);

@@ -25,6 +25,30 @@
 //   5 x-forward truncated to K rows, 1/n^3, P, integrating-factor
 //     AB2 (Euler on the first step)                                  A,U,H -> U,H
 #pragma once
+// launch-shape knobs of the z pass (threads per block cap, shared memory
+// cap in KiB, blocks per SM the register budget is sized for)
+#ifndef PS_ZP_MAXTHR
+#define PS_ZP_MAXTHR 384
+#endif
+#ifndef PS_ZP_SMEM_KB
+#define PS_ZP_SMEM_KB 100
+#endif
+#ifndef PS_ZP_MINB
+#define PS_ZP_MINB 0   // 0: 3 blocks per SM up to n = 256, 2 above
+#endif
+// 1: the first inverse stage reads the staged spectral lines directly
+// (two-for-one combination in registers); 0: a separate pass builds the
+// complex lines in the tiles first
+#ifndef PS_ZP_DIRECT
+#define PS_ZP_DIRECT 1
+#endif
+// tile width of the TMA-staged y passes (0 = automatic)
+#ifndef PS_TY_C
+#define PS_TY_C 0
+#endif
+#ifndef PS_TY_SMEM_KB
+#define PS_TY_SMEM_KB 116
+#endif
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
 
@@ -102,18 +126,52 @@ template <typename T, int N> struct Geo {
     // z pass: LZ lines per batch (even, divides n^2), 3 LZ G threads, two
     // staging buffers of the batch's six spectral lines plus the FFT tiles
     static constexpr int zsmem(int l) {
-        return (int)sizeof(C2) * (2 * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1);
+        return (int)sizeof(C2) * (2 * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1) + 128;
     }
     static constexpr int lz_pick() {
         int l = 2;
-        while (3 * (2 * l) * G <= 768 && zsmem(2 * l) <= 200 * 1024 && (N * N) % (2 * l) == 0) l *= 2;
+        while (3 * (2 * l) * G <= PS_ZP_MAXTHR && zsmem(2 * l) <= PS_ZP_SMEM_KB * 1024 && (N * N) % (2 * l) == 0)
+            l *= 2;
         return l;
     }
     static constexpr int LZ = lz_pick();
+    static constexpr int ZMINB = PS_ZP_MINB > 0 ? PS_ZP_MINB : (N <= 256 ? 3 : 2);
+    // TMA-staged y passes: K = kept x/y modes; inputs come in boxes of at
+    // most 256 rows (NBOX boxes of BR rows cover R rows)
+    static constexpr int K = 2 * ((N - 1) / 3) + 1;
+    static constexpr int nbox(int r) { return (r + 255) / 256; }
+    static constexpr int brows(int r) { return (r + nbox(r) - 1) / nbox(r); }
+    // smem rows between box starts: every box lands 128-byte aligned
+    static constexpr int bpitch(int r, int c) {
+        const int q = 128 / (c * (int)sizeof(C2)) > 0 ? 128 / (c * (int)sizeof(C2)) : 1;
+        return (brows(r) + q - 1) / q * q;
+    }
+    static constexpr int y2_smem(int c) {   // y inverse: 2 staging (K rows) + work tile (N rows)
+        return (int)sizeof(C2) * c * (2 * nbox(K) * bpitch(K, c) + N) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
+    }
+    static constexpr int y4_smem(int c) {   // y forward: 2 staging tiles of N rows, transformed in place
+        return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c)) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
+    }
+    static constexpr int pick_c(int which) {
+        if (PS_TY_C > 0) return PS_TY_C;
+        int c = CW;
+        while (c > 2 && (which == 2 ? y2_smem(c) : y4_smem(c)) > PS_TY_SMEM_KB * 1024) c /= 2;
+        return c;
+    }
+    static constexpr int CY2 = pick_c(2);
+    static constexpr int CY4 = pick_c(4);
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
 
 __device__ __forceinline__ int zaddr(int p, int line, int LP) { return line * LP + p + (p >> 4); }
+
+// Dynamic shared memory rounded up to a 128-byte boundary (TMA destinations
+// need it; kernels reserve 128 bytes of slack). The extern array's own
+// alignment is not relied on.
+__device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
+    const uint32_t a = smem_u32(raw);
+    return raw + ((128u - (a & 127u)) & 127u);
+}
 
 template <typename C2>
 __device__ __forceinline__ void load_tw(C2* s, const C2* g, int n) {
@@ -215,7 +273,7 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // per line pair; the result, truncated to kz < Kz, overwrites fields 0..2 of
 // B (only this batch's lines, whose input is already in shared memory).
 template <typename T, int N>
-__global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, 1)
+__global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
         const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
         int* __restrict__ err) {
@@ -225,7 +283,11 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     constexpr int nbatch = N * N / LZ;
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* stage = reinterpret_cast<C2*>(smraw);           // [2][6][LZ][KZP]
+    C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][6][LZ][KZP]
+    if (smem_u32(stage) & 127u) {   // never expected: refuse to start copies
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
     C2* tiles = stage + 2 * 6 * LZ * KZP;                // [LZ][3][LP]
     C2* tw = tiles + 3 * LZ * LP;
     __shared__ __align__(8) uint64_t bar[2];
@@ -271,6 +333,28 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             break;
         }
         const C2* st = stage + (size_t)buf * 6 * LZ * KZP;
+#if PS_ZP_DIRECT
+        {
+            const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
+            const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
+            const int tbase = (int)(tile(pl, pr) - tiles);
+            auto addr = [&](int p) { return tbase + zad(p); };
+            auto load = [&](int q) -> C2 {
+                if (q < Kz) {
+                    C2 a = fa[q], c = fb[q];
+                    if (q == 0) { a.y = 0; c.y = 0; }
+                    return cmk<C2>(a.x - c.y, a.y + c.x);          // A + i B
+                }
+                if (q > N - Kz) {
+                    const C2 a = fa[N - q], c = fb[N - q];
+                    return cmk<C2>(a.x + c.y, c.x - a.y);          // conj(A) + i conj(B)
+                }
+                return cmk<C2>((T)0, (T)0);
+            };
+            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
+            LineFFT<T, N, 1>::template run<false>(tiles, tw, addr, g, load, store);
+        }
+#else
         // spectral lines -> two-for-one complex lines in the tiles
         for (int idx = threadIdx.x; idx < 3 * LZ * N; idx += blockDim.x) {
             const int q = idx % N, lp = idx / N, l = lp / 3, p = lp % 3;
@@ -295,6 +379,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
             LineFFT<T, N, 1>::template run<true>(tiles, tw, addr, g, noload, store);
         }
+#endif
         __syncthreads();
         double fm[6] = {0, 0, 0, 0, 0, 0};
         bool touched = false;
@@ -518,6 +603,151 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
                 H[f * FS + o] = nn[f];
             }
         }
+    }
+}
+
+// --------------------------------------------- TMA-staged y passes
+// Persistent blocks walk a list of items (x plane, kz tile of CT columns,
+// field); each item's input tile arrives by tiled TMA copies into one of two
+// staging buffers while the previous item is transformed.
+
+// pass 2: y-inverse of the six fields, A (kept ky rows) -> B (all y rows).
+// tm: A as a 2-D array of 6 n K rows of 2 Kzp reals.
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::CY2 * Geo<T, N>::G)
+k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg,
+           int* __restrict__ err) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int CT = GE::CY2, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
+    constexpr int NTZ = KZP / CT;
+    constexpr int NITEM = N * NTZ * 6;
+    constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
+    if (smem_u32(S) & 127u) {   // never expected: refuse to start copies
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* W = S + 2 * RS * CT;                              // [N][CT]
+    C2* tw = W + N * CT;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int col = threadIdx.x % CT, g = threadIdx.x / CT;
+    const int mmax = kp.mmax, Kz = kp.Kz;
+    const size_t BS = (size_t)N * N * KZP;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, GE::tw_n);
+    __syncthreads();
+    auto issue = [&](int i, int buf) {  // one thread
+        const int f = i % 6, t = i / 6, x = t / NTZ, czt = t % NTZ;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
+        for (int b = 0; b < NBOX; ++b)
+            tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * N + x) * K + b * BR, &bar[buf]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < NITEM) issue(blockIdx.x, 0);
+    auto addr = [&](int p) { return p * CT + col; };
+    int it = 0;
+    for (int i = blockIdx.x; i < NITEM; i += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = i + (int)gridDim.x < NITEM;
+        if (threadIdx.x == 0 && more) issue(i + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const int f = i % 6, t = i / 6, x = t / NTZ, czt = t % NTZ;
+        const int cz = czt * CT + col;
+        const bool okz = cz < Kz;
+        const C2* Sb = S + (size_t)buf * RS * CT;
+        auto load = [&](int q) -> C2 {
+            const int m = mode_of(q, N);
+            if (m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
+            const int c = cidx_of(m, K);
+            return Sb[((c / BR) * BP + c % BR) * CT + col];
+        };
+        auto store = [&](int y, C2 v) {
+            if (okz) B[f * BS + ((size_t)x * N + y) * KZP + cz] = v;
+        };
+        LineFFT<T, N, 1>::template run<false>(W, tw, addr, g, load, store);
+        __syncthreads();
+    }
+}
+
+// pass 4: y-forward of the three fields, B (all y rows) -> A (kept ky rows).
+// tm: B as a 2-D array of 6 n n rows of 2 Kzp reals.
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::CY4 * Geo<T, N>::G)
+k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
+           int* __restrict__ err) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int CT = GE::CY4, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
+    static_assert(NBOX == 1 || BR == BP, "y-forward staging must be contiguous in y");
+    constexpr int NTZ = KZP / CT;
+    constexpr int NITEM = N * NTZ * 3;
+    constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
+    if (smem_u32(S) & 127u) {   // never expected: refuse to start copies
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* tw = S + 2 * RS * CT;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int col = threadIdx.x % CT, g = threadIdx.x / CT;
+    const int mmax = kp.mmax, Kz = kp.Kz;
+    const size_t AS = (size_t)N * K * KZP;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, GE::tw_n);
+    __syncthreads();
+    auto issue = [&](int i, int buf) {  // one thread
+        const int f = i % 3, t = i / 3, x = t / NTZ, czt = t % NTZ;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
+        for (int b = 0; b < NBOX; ++b)
+            tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * N + x) * N + b * BR, &bar[buf]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < NITEM) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int i = blockIdx.x; i < NITEM; i += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = i + (int)gridDim.x < NITEM;
+        if (threadIdx.x == 0 && more) issue(i + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const int f = i % 3, t = i / 3, x = t / NTZ, czt = t % NTZ;
+        const int cz = czt * CT + col;
+        const bool okz = cz < Kz;
+        C2* Sb = S + (size_t)buf * RS * CT;
+        auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
+        auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
+        auto store = [&](int q, C2 v) {
+            const int m = mode_of(q, N);
+            if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * KZP + cz] = v;
+        };
+        LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+        __syncthreads();
     }
 }
 
