@@ -37,6 +37,8 @@ struct ps_ctx {
     bool mask_init;           // rasteriser keys initialised
     bool mask_dense_dirty;    // chi/u_s may be nonzero outside the touched list
     CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
+    CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
+    CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
     int nstep;
     int has_velocity;
     // per-pass timing: a ring of events, kTimingRing steps deep
@@ -123,6 +125,22 @@ bool encode_rows(CUtensorMap* tm, void* base, int fp64, size_t rows, int Kzp, in
     cuuint32_t box[2] = {(cuuint32_t)(2 * bc), (cuuint32_t)br};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(tm, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 3-D map {2 Kzp reals, d1 rows of stride Kzp complex, d2 planes of stride
+// d1 Kzp complex}, box of `bc` complex columns x 1 x `br` planes.
+bool encode_planes(CUtensorMap* tm, void* base, int fp64, int Kzp, size_t d1, size_t d2, int bc, int br) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const size_t er = fp64 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * Kzp), (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)(2 * Kzp * er), (cuuint64_t)(d1 * 2 * Kzp * er)};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * bc), 1u, (cuuint32_t)br};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(tm, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -239,7 +257,7 @@ __global__ void k_diag(KP kp, const cplx<T>* __restrict__ U, double* __restrict_
         const int cz = (int)(i % Kz);
         const size_t r = i / Kz;
         const int cy = (int)(r % K), cx = (int)(r / K);
-        const size_t o = ((size_t)cx * K + cy) * Kzp + cz;
+        const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
         const double kx = kp.ks * cmode_of(cx, mm, K), ky = kp.ks * cmode_of(cy, mm, K), kz = kp.ks * cz;
         double s = 0.0, dr = 0.0, di = 0.0;
         const double kk[3] = {kx, ky, kz};
@@ -431,12 +449,20 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
         if (!encode_rows(&c->tmA, c->b.A, c->fp64, (size_t)6 * n * Kk, kp.Kzp, ops->cy2, ops->br2) ||
-            !encode_rows(&c->tmB, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4, ops->br4)) {
+            !encode_rows(&c->tmB, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4, ops->br4) ||
+            !encode_rows(&c->tmU, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2) ||
+            !encode_planes(&c->tmA5, c->b.A, c->fp64, kp.Kzp, (size_t)Kk, (size_t)6 * n, ops->cx5, ops->br4) ||
+            !encode_rows(&c->tmUp, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
+            !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2)) {
             delete c;
             return PS_ECUDA;
         }
         c->b.tmA = &c->tmA;
         c->b.tmB = &c->tmB;
+        c->b.tmU = &c->tmU;
+        c->b.tmA5 = &c->tmA5;
+        c->b.tmUp = &c->tmUp;
+        c->b.tmHp = &c->tmHp;
     }
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;

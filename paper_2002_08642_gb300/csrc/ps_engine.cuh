@@ -4,6 +4,13 @@
 #pragma once
 #include "ps_kernels.cuh"
 
+#ifndef PS_X1_OLD
+#define PS_X1_OLD 0
+#endif
+#ifndef PS_X5_OLD
+#define PS_X5_OLD 0
+#endif
+
 namespace ps {
 
 struct Bufs {
@@ -21,11 +28,16 @@ struct Bufs {
     int* err;        // device error flag (bounded waits that gave up)
     const CUtensorMap* tmA;  // A as rows of 2 Kzp reals (y-inverse input)
     const CUtensorMap* tmB;  // B as rows of 2 Kzp reals (y-forward input)
+    const CUtensorMap* tmU;  // U as rows of 2 Kzp reals (x-inverse input)
+    const CUtensorMap* tmA5; // A as {2 Kzp, K, 6 n} (x-forward input)
+    const CUtensorMap* tmUp; // U, H as rows of 2 Kzp reals, x-forward box (L2 prefetch)
+    const CUtensorMap* tmHp;
 };
 
 struct Ops {
     int n, C, C5, LY, G;
     int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
+    int cx1, cx5;             // TMA box widths of the x passes (heights br2, br4)
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
     cudaError_t (*prepare)(int nsm, int* zblocks);
     // ev (nullable): 6 events recorded before pass 1 and after each pass
@@ -63,6 +75,18 @@ template <typename T, int N> struct Engine {
         static int g = 0;
         return g;
     }
+    static int& x1grid() {
+        static int g = 0;
+        return g;
+    }
+    static int& x5grid() {
+        static int g = 0;
+        return g;
+    }
+    static constexpr size_t sm_x1 = (size_t)GE::y2_smem(GE::CX1);
+    static constexpr size_t sm_x5t = (size_t)GE::x5_smem(GE::CX5);
+    static constexpr int thr_x1 = GE::CX1 * GE::G;
+    static constexpr int thr_x5 = GE::CX5 * GE::G;
     static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2);
     static constexpr size_t sm_y4 = (size_t)GE::y4_smem(GE::CY4);
     static constexpr int thr_y2 = GE::CY2 * GE::G;
@@ -92,6 +116,13 @@ template <typename T, int N> struct Engine {
         y2grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N>, thr_y4, sm_y4))) return e;
         y4grid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = attr(k_xinv_tma<T, N>, sm_x1))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N>, thr_x1, sm_x1))) return e;
+        x1grid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
+        x5grid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
     }
 
@@ -103,7 +134,11 @@ template <typename T, int N> struct Engine {
     static cudaError_t step(const KP& kp, const Bufs& b, int first, cudaStream_t s, cudaEvent_t* ev) {
         const C2* tw = (const C2*)b.tw;
         if (ev) cudaEventRecord(ev[0], s);
+#if PS_X1_OLD
         k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
+#else
+        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
+#endif
         if (ev) cudaEventRecord(ev[1], s);
         k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, kp, (C2*)b.B, tw, b.err);
         if (ev) cudaEventRecord(ev[2], s);
@@ -112,8 +147,13 @@ template <typename T, int N> struct Engine {
         if (ev) cudaEventRecord(ev[3], s);
         k_yfwd_tma<T, N><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, kp, (C2*)b.A, tw, b.err);
         if (ev) cudaEventRecord(ev[4], s);
+#if PS_X5_OLD
         k_xfwd<T, N, 0><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
                                                                  (const T*)b.Ex, (const T*)b.Ez, first, tw);
+#else
+        k_xfwd_tma<T, N, 0><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
+                                                            (const T*)b.Ex, (const T*)b.Ez, first, tw, b.err);
+#endif
         if (ev) cudaEventRecord(ev[5], s);
         return cudaGetLastError();
     }
@@ -122,8 +162,8 @@ template <typename T, int N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, tw);
         k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
-        k_xfwd<T, N, 1><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
-                                                                 (const T*)b.Ex, (const T*)b.Ez, 0, tw);
+        k_xfwd_tma<T, N, 1><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
+                                                            (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         return cudaGetLastError();
     }
 
@@ -139,6 +179,7 @@ template <typename T, int N> struct Engine {
         Ops o;
         o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
         o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
+        o.cx1 = GE::CX1; o.cx5 = GE::CX5;
         o.zblocks = 0;
         o.prepare = &prepare;
         o.step = &step;

@@ -193,8 +193,15 @@ template <typename T, int N, int SIGN> struct LineFFT {
     static constexpr int S = n_stages(N);
     static constexpr int R0 = radix_at(N, 0);
     static constexpr int G = N / R0;
+    // last stage: radix, butterflies per thread; SLOTS outputs per thread
+    static constexpr int RL = radix_at(N, S - 1);
+    static constexpr int NBL = (N / RL + G - 1) / G;
+    static constexpr int SLOTS = NBL * RL;
 
-    template <int s, bool FROM_TILE, class Addr, class Load, class Store>
+    // BU: the last stage calls store(slot, position, value) with the
+    // compile-time slot b * RL + u (butterfly b, output u), so a caller can
+    // keep a thread's outputs in registers; otherwise store(position, value).
+    template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
                                                  const Load& load, const Store& store, bool on = true) {
         constexpr int r = radix_at(N, s);
@@ -222,14 +229,18 @@ template <typename T, int N, int SIGN> struct LineFFT {
                 v[t] = x;
             }
         };
-        auto scatter = [&](int j, C* v) {
+        auto scatter = [&](int j, C* v, int b) {
             const int k = j % Ls;
             Dft<r, SIGN, C>::run(v);
 #pragma unroll
             for (int u = 0; u < r; ++u) {
                 const int o = (j - k) * r + k + u * Ls;
-                if constexpr (last) store(o, v[u]);
-                else tile[addr(o)] = v[u];
+                if constexpr (last) {
+                    if constexpr (BU) store(b * r + u, o, v[u]);
+                    else store(o, v[u]);
+                } else {
+                    tile[addr(o)] = v[u];
+                }
             }
         };
         if constexpr (from_tile && !last) {
@@ -244,7 +255,18 @@ template <typename T, int N, int SIGN> struct LineFFT {
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int j = g + b * G;
-                if (on && (NB * G == NBF || j < NBF)) scatter(j, v[b]);
+                if (on && (NB * G == NBF || j < NBF)) scatter(j, v[b], b);
+            }
+        } else if constexpr (BU && last) {
+            // one butterfly at a time, unrolled so that slots are constants
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int j = g + b * G;
+                if (on && (NB * G == NBF || j < NBF)) {
+                    C v[r];
+                    gather(j, v);
+                    scatter(j, v, b);
+                }
             }
         } else {
             // reads from the functor, or the last stage (each butterfly reads
@@ -255,18 +277,24 @@ template <typename T, int N, int SIGN> struct LineFFT {
                 if (on && (NB * G == NBF || j < NBF)) {
                     C v[r];
                     gather(j, v);
-                    scatter(j, v);
+                    scatter(j, v, b);
                 }
             }
         }
         if constexpr (!last) __syncthreads();
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE>(tile, tw, addr, g, load, store, on);
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run(C* tile, const C* tw, const Addr& addr, int g,
                                                const Load& load, const Store& store) {
         stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true);
+    }
+    // Last-stage outputs delivered as store(slot, position, value).
+    template <bool FROM_TILE, class Addr, class Load, class Store>
+    static __device__ __forceinline__ void run_bu(C* tile, const C* tw, const Addr& addr, int g,
+                                                  const Load& load, const Store& store) {
+        stage<0, FROM_TILE, true>(tile, tw, addr, g, load, store, true);
     }
     // Same, but threads with on == false only take part in the barriers.
     template <bool FROM_TILE, class Addr, class Load, class Store>

@@ -4,7 +4,8 @@
 //
 // Storage (element = complex T unless stated):
 //   U, H   spectral velocity c_k = DFT(u)_k / n^3 and AB2 history N^{n-1},
-//          3 x [K][K][Kzp], only the modes the 2/3 rule keeps:
+//          3 x [K (ky)][K (kx)][Kzp] (an x line of fixed ky, kz is a
+//          contiguous block), only the modes the 2/3 rule keeps:
 //          x/y index c in [0, K) <-> mode m = c (c <= mmax) or c - K,
 //          z index c in [0, Kz) <-> mode m = c; K = 2 mmax + 1, Kz = mmax + 1,
 //          mmax = (n - 1) / 3, Kzp = Kz rounded up to the tile width.
@@ -46,8 +47,17 @@
 #ifndef PS_TY_C
 #define PS_TY_C 0
 #endif
-#ifndef PS_TY_SMEM_KB
-#define PS_TY_SMEM_KB 116
+#ifndef PS_Y2_SMEM_KB
+#define PS_Y2_SMEM_KB 226
+#endif
+#ifndef PS_Y4_SMEM_KB
+#define PS_Y4_SMEM_KB 226
+#endif
+#ifndef PS_X1_SMEM_KB
+#define PS_X1_SMEM_KB 64
+#endif
+#ifndef PS_X5_SMEM_KB
+#define PS_X5_SMEM_KB 200
 #endif
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
@@ -152,14 +162,23 @@ template <typename T, int N> struct Geo {
     static constexpr int y4_smem(int c) {   // y forward: 2 staging tiles of N rows, transformed in place
         return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c)) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
-    static constexpr int pick_c(int which) {
+    static constexpr int x5_smem(int c) {   // x forward: 2 staging tiles (N rows) + 3 kept-mode result tiles
+        return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c) + 3 * K) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
+    }
+    // widest tile (at most cmax complex, at least 2) whose shared memory fits
+    static constexpr int pick_c(int which, int kb, int cmax) {
         if (PS_TY_C > 0) return PS_TY_C;
-        int c = CW;
-        while (c > 2 && (which == 2 ? y2_smem(c) : y4_smem(c)) > PS_TY_SMEM_KB * 1024) c /= 2;
+        int c = cmax < CW ? cmax : CW;
+        while (c > 2 && (which == 2 ? y2_smem(c) : which == 4 ? y4_smem(c) : x5_smem(c)) > kb * 1024) c /= 2;
         return c;
     }
-    static constexpr int CY2 = pick_c(2);
-    static constexpr int CY4 = pick_c(4);
+    // budgets measured on GB300 (FP32 and FP64 alike): the y passes and the
+    // x-forward pass prefer one wide tile per SM, the x-inverse (two register
+    // sets of outputs per thread) several narrow ones
+    static constexpr int CY2 = pick_c(2, PS_Y2_SMEM_KB, 16);
+    static constexpr int CY4 = pick_c(4, PS_Y4_SMEM_KB, 16);
+    static constexpr int CX1 = pick_c(2, PS_X1_SMEM_KB, 16);
+    static constexpr int CX5 = pick_c(5, PS_X5_SMEM_KB, 128 / 16);
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
 
@@ -207,7 +226,7 @@ k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx
         auto load = [&](int q) -> C2 {
             const int m = mode_of(q, N);
             if (!okz || m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
-            const size_t o = ((size_t)cidx_of(m, K) * K + cy) * Kzp + cz;
+            const size_t o = ((size_t)cy * K + cidx_of(m, K)) * Kzp + cz;
             const T kx = (T)(kp.ks * m);
             if (f < 3) return U[f * FS + o];
             if (f == 3) {  // i (ky uz - kz uy)
@@ -580,7 +599,7 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         } else if (MODE == 0 && !kp.mean_free) {
             n0 = n1 = n2 = cmk<C2>((T)0, (T)0);
         }
-        const size_t o = ((size_t)cx * K + cy) * Kzp + czz;
+        const size_t o = ((size_t)cy * K + cx) * Kzp + czz;
         if constexpr (MODE == 1) {
             U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
             const C2 z = cmk<C2>((T)0, (T)0);
@@ -747,6 +766,262 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * KZP + cz] = v;
         };
         LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+        __syncthreads();
+    }
+}
+
+// pass 1 (TMA-staged): x-inverse of u and omega = curl u with five
+// transforms per (cy, kz tile): Ux, Uy, Dx Uy = F[i kx u_y], Uz, Dx Uz.
+// Along an x line ky and kz are constant, so after the x transform
+//   w_x = i (ky Uz - kz Uy),  w_y = i kz Ux - Dx Uz,  w_z = Dx Uy - i ky Ux;
+// a thread keeps its last-stage outputs of Ux and Uy in registers until the
+// transforms that need them. Inputs arrive field by field (x, y, z) by TMA.
+// tm: U as 2-D rows of 2 Kzp reals, row (f K + cy) K + cx.
+template <typename T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::CX1 * Geo<T, N>::G)
+k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
+           int* __restrict__ err) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    using FFT = LineFFT<T, N, 1>;
+    constexpr int CT = GE::CX1, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
+    constexpr int NTZ = KZP / CT;
+    constexpr int NTILE = K * NTZ;
+    constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
+    if (smem_u32(S) & 127u) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* W = S + 2 * RS * CT;                              // [N][CT]
+    C2* tw = W + N * CT;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int col = threadIdx.x % CT, g = threadIdx.x / CT;
+    const int mmax = kp.mmax, Kz = kp.Kz;
+    const size_t AS = (size_t)N * K * KZP;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, GE::tw_n);
+    __syncthreads();
+    // load L: tile iteration L / 3, field L % 3
+    auto issue = [&](int L) {  // one thread
+        const int t = blockIdx.x + (L / 3) * gridDim.x, f = L % 3, buf = L & 1;
+        if (t >= NTILE) return;
+        const int cy = t / NTZ, czt = t % NTZ;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
+        for (int b = 0; b < NBOX; ++b)
+            tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * K + cy) * K + b * BR, &bar[buf]);
+    };
+    if (threadIdx.x == 0) issue(0);
+    auto addr = [&](int p) { return p * CT + col; };
+    C2 R1[FFT::SLOTS], R2[FFT::SLOTS];
+    int ti = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
+        const int cy = t / NTZ, czt = t % NTZ;
+        const int cz = czt * CT + col;
+        const bool okz = cz < Kz;
+        const T ky = (T)(kp.ks * cmode_of(cy, mmax, K));
+        const T kz = (T)(kp.ks * cz);
+        C2* out = A + ((size_t)cy) * KZP + cz;   // + f AS + x K KZP
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f) {
+            const int L = 3 * ti + f, buf = L & 1;
+            if (threadIdx.x == 0) issue(L + 1);
+            const bool ok = mbar_wait(&bar[buf], (uint32_t)((L >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(err, 1);
+                    mbar_wait(&bar[buf ^ 1], (uint32_t)(((L + 1) >> 1) & 1));
+                }
+                stop = true;
+                break;
+            }
+            const C2* Sb = S + (size_t)buf * RS * CT;
+#pragma unroll 1
+            for (int d = 0; d < (f == 0 ? 1 : 2); ++d) {
+                // d = 1: the x derivative i kx u_f
+                auto load = [&](int q) -> C2 {
+                    const int m = mode_of(q, N);
+                    if (m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
+                    const int c = cidx_of(m, K);
+                    const C2 v = Sb[((c / BR) * BP + c % BR) * CT + col];
+                    if (d == 0) return v;
+                    const T kx = (T)(kp.ks * m);
+                    return cmk<C2>(-kx * v.y, kx * v.x);
+                };
+                auto store = [&](int slot, int x, C2 v) {
+                    C2* o = out + (size_t)x * K * KZP;
+                    if (f == 0) {                       // Ux
+                        R1[slot] = v;
+                        if (okz) o[0] = v;
+                    } else if (f == 1 && d == 0) {      // Uy
+                        R2[slot] = v;
+                        if (okz) o[AS] = v;
+                    } else if (f == 1) {                // w_z = Dx Uy - i ky Ux
+                        const C2 u = R1[slot];
+                        if (okz) o[5 * AS] = cmk<C2>(v.x + ky * u.y, v.y - ky * u.x);
+                    } else if (d == 0) {                // Uz; w_x = i (ky Uz - kz Uy)
+                        const C2 u = R2[slot];
+                        if (okz) {
+                            o[2 * AS] = v;
+                            o[3 * AS] = cmk<C2>(-(ky * v.y - kz * u.y), ky * v.x - kz * u.x);
+                        }
+                    } else {                            // w_y = i kz Ux - Dx Uz
+                        const C2 u = R1[slot];
+                        if (okz) o[4 * AS] = cmk<C2>(-kz * u.y - v.x, kz * u.x - v.y);
+                    }
+                };
+                FFT::template run_bu<false>(W, tw, addr, g, load, store);
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// pass 5 (TMA-staged): x-forward of the three fields of n, truncation to the
+// kept kx, 1/n^3, Leray projection and the integrating-factor AB2 (Euler on
+// the first step) update of U and H. MODE 1 instead sets U to the projected
+// field (mean kept) and clears H. Each field is transformed in place in its
+// staging buffer; kept outputs go to three result tiles.
+// tm: A as 3-D {2 Kzp reals, K (cy), 3 n (f n + x)}.
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(Geo<T, N>::CX5 * Geo<T, N>::G)
+k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmu,
+           const __grid_constant__ CUtensorMap tmh, KP kp, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H,
+           const T* __restrict__ Ex, const T* __restrict__ Ez, int first, const cplx<T>* __restrict__ twg,
+           int* __restrict__ err) {
+    using C2 = cplx<T>;
+    using GE = Geo<T, N>;
+    constexpr int CT = GE::CX5, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
+    static_assert(NBOX == 1 || BR == BP, "x-forward staging must be contiguous in x");
+    constexpr int NTZ = KZP / CT;
+    constexpr int NTILE = K * NTZ;
+    constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
+    if (smem_u32(S) & 127u) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* Rt = S + 2 * RS * CT;                             // [3][K][CT]
+    C2* tw = Rt + 3 * K * CT;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int col = threadIdx.x % CT, g = threadIdx.x / CT;
+    const int mmax = kp.mmax, Kz = kp.Kz;
+    const size_t FS = (size_t)K * K * KZP;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, GE::tw_n);
+    __syncthreads();
+    auto issue = [&](int L) {  // one thread
+        const int t = blockIdx.x + (L / 3) * gridDim.x, f = L % 3, buf = L & 1;
+        if (t >= NTILE) return;
+        const int cy = t / NTZ, czt = t % NTZ;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
+        for (int b = 0; b < NBOX; ++b)
+            tma_load_3d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, cy, f * N + b * BR, &bar[buf]);
+    };
+    if (threadIdx.x == 0) issue(0);
+    const T s = (T)kp.ks;
+    const T invn3 = (T)kp.invn3;
+    const T dt = (T)kp.dt;
+    int ti = 0;
+    bool stop = false;
+    constexpr int NBK = GE::nbox(K), BRK = GE::brows(K);
+    for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
+        const int cy = t / NTZ, czt = t % NTZ;
+        // U and H of this tile are read only after the three transforms:
+        // start pulling them into L2 now
+        if (MODE == 0 && threadIdx.x < 3 * NBK) {
+            const int f = threadIdx.x / NBK, b = threadIdx.x % NBK;
+            tma_prefetch_2d(&tmu, 2 * czt * CT, (f * K + cy) * K + b * BRK);
+            if (!first) tma_prefetch_2d(&tmh, 2 * czt * CT, (f * K + cy) * K + b * BRK);
+        }
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f) {
+            const int L = 3 * ti + f, buf = L & 1;
+            if (threadIdx.x == 0) issue(L + 1);
+            const bool ok = mbar_wait(&bar[buf], (uint32_t)((L >> 1) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicExch(err, 1);
+                    mbar_wait(&bar[buf ^ 1], (uint32_t)(((L + 1) >> 1) & 1));
+                }
+                stop = true;
+                break;
+            }
+            C2* Sb = S + (size_t)buf * RS * CT;
+            C2* Rf = Rt + f * K * CT;
+            auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
+            auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
+            auto store = [&](int q, C2 v) {
+                const int m = mode_of(q, N);
+                if (m <= mmax && m >= -mmax) Rf[cidx_of(m, K) * CT + col] = v;
+            };
+            LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+            __syncthreads();
+        }
+        if (stop) break;
+        const T my = (T)cmode_of(cy, mmax, K);
+        const T ey = Ex[cy];
+        for (int idx = threadIdx.x; idx < K * CT; idx += blockDim.x) {
+            const int cx = idx / CT, c = idx % CT;
+            const int czz = czt * CT + c;
+            if (czz >= Kz) continue;
+            const int mx = cmode_of(cx, mmax, K);
+            C2 n0 = Rt[idx], n1 = Rt[K * CT + idx], n2 = Rt[2 * K * CT + idx];
+            n0.x *= invn3; n0.y *= invn3;
+            n1.x *= invn3; n1.y *= invn3;
+            n2.x *= invn3; n2.y *= invn3;
+            const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+            const T k2 = kx * kx + ky * ky + kz * kz;
+            const bool zero = (mx == 0 && cy == 0 && czz == 0);
+            if (!zero) {
+                const T ik2 = (T)1 / k2;
+                const T dr = (kx * n0.x + ky * n1.x + kz * n2.x) * ik2;
+                const T di = (kx * n0.y + ky * n1.y + kz * n2.y) * ik2;
+                n0.x -= kx * dr; n0.y -= kx * di;
+                n1.x -= ky * dr; n1.y -= ky * di;
+                n2.x -= kz * dr; n2.y -= kz * di;
+            } else if (MODE == 0 && !kp.mean_free) {
+                n0 = n1 = n2 = cmk<C2>((T)0, (T)0);
+            }
+            const size_t o = ((size_t)cy * K + cx) * KZP + czz;
+            if constexpr (MODE == 1) {
+                U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
+                const C2 z = cmk<C2>((T)0, (T)0);
+                H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
+            } else {
+                const T E = Ex[cx] * ey * Ez[czz];
+                const C2 nn[3] = {n0, n1, n2};
+#pragma unroll
+                for (int ff = 0; ff < 3; ++ff) {
+                    const C2 u = U[ff * FS + o];
+                    C2 r;
+                    if (first) {
+                        r = cmk<C2>(E * (u.x + dt * nn[ff].x), E * (u.y + dt * nn[ff].y));
+                    } else {
+                        const C2 h = H[ff * FS + o];
+                        const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
+                        r = cmk<C2>(E * u.x + a3 * nn[ff].x - a2 * h.x, E * u.y + a3 * nn[ff].y - a2 * h.y);
+                    }
+                    U[ff * FS + o] = r;
+                    H[ff * FS + o] = nn[ff];
+                }
+            }
+        }
         __syncthreads();
     }
 }
