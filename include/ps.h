@@ -65,6 +65,8 @@ enum { PS_MEAN_FIXED = 0, PS_MEAN_FREE = 1 };
  *              grid point.
  *   mean_mode  PS_MEAN_FIXED: the k = 0 mode of the right-hand side is
  *              dropped (mean velocity fixed); PS_MEAN_FREE: kept.
+ *   with_adjoint  1: the workspace also holds the adjoint state and scratch
+ *              (six spectral state arrays and nine physical fields more).
  *   L, nu, eta, dt  box length, kinematic viscosity, penalization constant,
  *              time step (all > 0).
  *   tw, h      wing semi-thickness and smoothing semi-width of the mask.
@@ -75,6 +77,7 @@ typedef struct {
     int32_t precision;
     int32_t mask_profile;
     int32_t mean_mode;
+    int32_t with_adjoint;
     double L, nu, eta, dt;
     double tw, h;
     double x0[3];
@@ -156,6 +159,29 @@ ps_status ps_diagnostics(ps_ctx* ctx, double* energy, double* max_div);
 ps_status ps_state_size(const ps_ctx* ctx, size_t* bytes);
 ps_status ps_save_state(ps_ctx* ctx, void* buf_dev);
 ps_status ps_restore_state(ps_ctx* ctx, const void* buf_dev);
+
+/* Discrete adjoint (no counterpart in the paper: the exact transpose of the
+ * step's operations) for objectives J = sum_n (a_n . F^n + b_n . M^n), F^n,
+ * M^n the force and moment of step n (ps_forces). Needs with_adjoint = 1.
+ * ps_adjoint_reset zeroes the adjoint state (before the last step of a
+ * window is reversed). ps_adjoint_step reverses step n: the context must hold
+ * the forward state u^n (use ps_restore_state / ps_step to get there) and the
+ * mask chi^n, u_s^n of that step; dJdF = a_n, dJdM = b_n (host, 3 doubles
+ * each); first = 1 if step n was the integrating-factor Euler start step.
+ * It overwrites grad_chi_dev (n^3 real) and grad_us_dev (3*n^3 real) with
+ * dJ/dchi^n and dJ/du_s^n and updates the adjoint state. Asynchronous. */
+ps_status ps_adjoint_reset(ps_ctx* ctx);
+ps_status ps_adjoint_step(ps_ctx* ctx, const double dJdF[3], const double dJdM[3], int32_t first,
+                          void* grad_chi_dev, void* grad_us_dev);
+
+/* Vector-Jacobian product of the last ps_set_mask_from_nodes call: given
+ * dJ/dchi and dJ/du_s on the grid (caller device memory, context precision),
+ * ADDS dJ/dx^(w) of the wing-frame node positions to grad_xw_dev (n_nodes x 3
+ * double, caller device memory), holding each point's closest triangle fixed.
+ * The node/triangle arrays of that call must still be alive. Asynchronous;
+ * PS_ESTATE if the mask was set densely since. */
+ps_status ps_mask_nodes_vjp(ps_ctx* ctx, const void* grad_chi_dev, const void* grad_us_dev,
+                            double* grad_xw_dev);
 
 /* Per-pass device timing with CUDA events on the context's stream.
  * ps_timing_enable(ctx, 1) resets the accumulators and records events around

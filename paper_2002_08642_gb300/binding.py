@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "P
 
 class PsParams(ctypes.Structure):
     _fields_ = [("n", c_int32), ("precision", c_int32), ("mask_profile", c_int32), ("mean_mode", c_int32),
-                ("L", c_double), ("nu", c_double), ("eta", c_double), ("dt", c_double),
+                ("with_adjoint", c_int32), ("L", c_double), ("nu", c_double), ("eta", c_double), ("dt", c_double),
                 ("tw", c_double), ("h", c_double), ("x0", c_double * 3)]
 
 
@@ -56,6 +56,9 @@ _SIGS = {
     "ps_state_size": (c_int32, [c_void_p, _P(c_size_t)]),
     "ps_save_state": (c_int32, [c_void_p, c_void_p]),
     "ps_restore_state": (c_int32, [c_void_p, c_void_p]),
+    "ps_adjoint_reset": (c_int32, [c_void_p]),
+    "ps_adjoint_step": (c_int32, [c_void_p, _P(c_double), _P(c_double), c_int32, c_void_p, c_void_p]),
+    "ps_mask_nodes_vjp": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ps_timing_enable": (c_int32, [c_void_p, c_int32]),
     "ps_timing_read": (c_int32, [c_void_p, _P(c_double), _P(ctypes.c_int64), c_int32, _P(c_int32)]),
     "ps_timing_name": (ctypes.c_char_p, [c_int32]),
@@ -183,6 +186,20 @@ def ps_save_state(ctx, buf_ptr):
 
 def ps_restore_state(ctx, buf_ptr):
     check(lib().ps_restore_state(ctx, c_void_p(buf_ptr)), ctx)
+
+
+def ps_adjoint_reset(ctx):
+    check(lib().ps_adjoint_reset(ctx), ctx)
+
+
+def ps_adjoint_step(ctx, dJdF, dJdM, first, gchi_ptr, gus_ptr):
+    F = (c_double * 3)(*[float(v) for v in dJdF])
+    M = (c_double * 3)(*[float(v) for v in dJdM])
+    check(lib().ps_adjoint_step(ctx, F, M, 1 if first else 0, c_void_p(gchi_ptr), c_void_p(gus_ptr)), ctx)
+
+
+def ps_mask_nodes_vjp(ctx, gchi_ptr, gus_ptr, gxw_ptr):
+    check(lib().ps_mask_nodes_vjp(ctx, c_void_p(gchi_ptr), c_void_p(gus_ptr), c_void_p(gxw_ptr)), ctx)
 
 
 def ps_timing_enable(ctx, on):

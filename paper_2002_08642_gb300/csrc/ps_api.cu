@@ -16,6 +16,7 @@
 #include "ps.h"
 #include "ps_engine.cuh"
 #include "ps_mask.cuh"
+#include "ps_adjoint.cuh"
 
 using namespace ps;
 
@@ -39,6 +40,12 @@ struct ps_ctx {
     CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
     CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
+    // adjoint (with_adjoint): lam, mu, G, W, Ub, Wb spectral; u, w, nb physical
+    void* adj_spec[6];
+    void* adj_phys[3];
+    double* gX;               // rasteriser VJP scratch (n_nodes x 3)
+    MaskArgs last_mask;       // geometry of the last rasterisation
+    bool has_last_mask;
     int nstep;
     int has_velocity;
     // per-pass timing: a ring of events, kTimingRing steps deep
@@ -60,7 +67,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int tile_width(int fp64) { return fp64 ? 8 : 16; }
 
 struct Layout {
-    size_t U, H, A, B, chi, us, flag, tw, Ex, Ez, partial, out, err, mask, total;
+    size_t U, H, A, B, chi, us, flag, tw, Ex, Ez, partial, out, err, mask, adj_spec[6], adj_phys[3], gX, total;
     size_t ustate, mask_bytes;
 };
 
@@ -93,6 +100,9 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->err = take(256);
     L->mask_bytes = mask_workspace_bytes(n);
     L->mask = take(L->mask_bytes);
+    for (int i = 0; i < 6; ++i) L->adj_spec[i] = p->with_adjoint ? take(L->ustate) : 0;
+    for (int i = 0; i < 3; ++i) L->adj_phys[i] = p->with_adjoint ? take(3 * n3 * er) : 0;
+    L->gX = take((size_t)kMaskMaxNodes * 3 * sizeof(double));
     L->total = off;
     return true;
 }
@@ -160,6 +170,7 @@ ps_status check_params(const ps_params* p, std::string* why) {
     if (p->precision != PS_FP32 && p->precision != PS_FP64) { *why = "precision must be PS_FP32 or PS_FP64"; return PS_EINVAL; }
     if (p->mask_profile != PS_MASK_COS && p->mask_profile != PS_MASK_TANH) { *why = "bad mask_profile"; return PS_EINVAL; }
     if (p->mean_mode != PS_MEAN_FIXED && p->mean_mode != PS_MEAN_FREE) { *why = "bad mean_mode"; return PS_EINVAL; }
+    if (p->with_adjoint != 0 && p->with_adjoint != 1) { *why = "with_adjoint must be 0 or 1"; return PS_EINVAL; }
     if (!(p->L > 0) || !(p->nu >= 0) || !(p->eta > 0) || !(p->dt > 0) || !(p->h > 0) || !(p->tw >= 0)) {
         *why = "L, eta, dt, h must be > 0 and nu, tw >= 0";
         return PS_EINVAL;
@@ -360,6 +371,34 @@ template cudaError_t ps::rasterise<float>(const MaskArgs&, void*, void*, uint8_t
 template cudaError_t ps::rasterise<double>(const MaskArgs&, void*, void*, uint8_t*, unsigned char*, int, bool, bool,
                                            cudaStream_t, int*);
 
+template <typename T>
+static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* gus) {
+    using C2 = cplx<T>;
+    cudaStream_t s = c->stream;
+    const int nb = 4 * 152;
+    C2* lam = (C2*)c->adj_spec[0];
+    C2* mu = (C2*)c->adj_spec[1];
+    C2* G = (C2*)c->adj_spec[2];
+    C2* W = (C2*)c->adj_spec[3];
+    C2* Ub = (C2*)c->adj_spec[4];
+    C2* Wb = (C2*)c->adj_spec[5];
+    T* up = (T*)c->adj_phys[0];
+    T* wp = (T*)c->adj_phys[1];
+    T* np_ = (T*)c->adj_phys[2];
+    cudaError_t e;
+    k_adj_spec1<T><<<nb, 256, 0, s>>>(c->kp, lam, mu, G, (const T*)c->b.Ex, (const T*)c->b.Ez, aw.first);
+    k_curl_spec<T><<<nb, 256, 0, s>>>(c->kp, (const C2*)c->b.U, W);
+    if ((e = c->ops->inv3(c->kp, c->b, c->b.U, up, s)) != cudaSuccess) return e;
+    if ((e = c->ops->inv3(c->kp, c->b, W, wp, s)) != cudaSuccess) return e;
+    if ((e = c->ops->inv3(c->kp, c->b, G, np_, s)) != cudaSuccess) return e;
+    k_adj_point<T><<<nb * 2, 256, 0, s>>>(c->kp, aw, up, wp, np_, (const T*)c->b.chi, (const T*)c->b.us, (T*)gchi,
+                                          (T*)gus, c->p.n);
+    if ((e = c->ops->fwd3(c->kp, c->b, up, Ub, s)) != cudaSuccess) return e;
+    if ((e = c->ops->fwd3(c->kp, c->b, wp, Wb, s)) != cudaSuccess) return e;
+    k_adj_spec2<T><<<nb, 256, 0, s>>>(c->kp, lam, Ub, Wb);
+    return cudaGetLastError();
+}
+
 extern "C" {
 
 ps_status ps_supported_n(int32_t* out, int32_t cap, int32_t* count) {
@@ -440,6 +479,9 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     c->out = (double*)(w + L.out);
     c->b.err = (int*)(w + L.err);
     c->mask_ws = w + L.mask;
+    for (int i = 0; i < 6; ++i) c->adj_spec[i] = p->with_adjoint ? (void*)(w + L.adj_spec[i]) : nullptr;
+    for (int i = 0; i < 3; ++i) c->adj_phys[i] = p->with_adjoint ? (void*)(w + L.adj_phys[i]) : nullptr;
+    c->gX = (double*)(w + L.gX);
     c->mask_ws_bytes = L.mask_bytes;
 
     int nsm = 0;
@@ -524,6 +566,7 @@ ps_status ps_set_mask(ps_ctx* c, const void* chi, const void* us) {
     else k_line_flags<float><<<(unsigned)((lines + per - 1) / per), 32 * per, 0, c->stream>>>((const float*)c->b.chi, c->b.flag, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ps_set_mask flags");
     c->mask_dense_dirty = true;
+    c->has_last_mask = false;
     return PS_OK;
 }
 
@@ -577,6 +620,8 @@ ps_status ps_set_mask_from_nodes(ps_ctx* c, const double* xw, const double* vw, 
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->mask_par = np;
     c->mask_init = true;
+    c->last_mask = a;
+    c->has_last_mask = true;
     c->mask_dense_dirty = (a.profile == PS_MASK_TANH);
     return PS_OK;
 }
@@ -673,6 +718,56 @@ ps_status ps_restore_state(ps_ctx* c, const void* buf) {
     if (s != PS_OK) return s;
     c->nstep = (int)hdr[0];
     c->has_velocity = (int)hdr[1];
+    return PS_OK;
+}
+
+ps_status ps_adjoint_reset(ps_ctx* c) {
+    if (!c) return PS_EINVAL;
+    if (!c->p.with_adjoint) return fail(c, PS_ESTATE, "ps_adjoint_reset: context created without with_adjoint");
+    DeviceGuard dg(c->device);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->adj_spec[0], 0, c->ustate, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->adj_spec[1], 0, c->ustate, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ps_adjoint_reset");
+    return PS_OK;
+}
+
+ps_status ps_adjoint_step(ps_ctx* c, const double dJdF[3], const double dJdM[3], int32_t first, void* grad_chi_dev,
+                          void* grad_us_dev) {
+    if (!c) return PS_EINVAL;
+    if (!c->p.with_adjoint) return fail(c, PS_ESTATE, "ps_adjoint_step: context created without with_adjoint");
+    if (!dJdF || !dJdM || !grad_chi_dev || !grad_us_dev)
+        return fail(c, PS_EINVAL, "ps_adjoint_step: null argument");
+    DeviceGuard dg(c->device);
+    AdjW aw;
+    for (int i = 0; i < 3; ++i) { aw.a[i] = dJdF[i]; aw.b[i] = dJdM[i]; }
+    aw.first = first ? 1 : 0;
+    cudaError_t e = c->fp64 ? adjoint_step_t<double>(c, aw, grad_chi_dev, grad_us_dev)
+                            : adjoint_step_t<float>(c, aw, grad_chi_dev, grad_us_dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_adjoint_step");
+    return PS_OK;
+}
+
+ps_status ps_mask_nodes_vjp(ps_ctx* c, const void* grad_chi_dev, const void* grad_us_dev, double* grad_xw_dev) {
+    if (!c) return PS_EINVAL;
+    if (!grad_chi_dev || !grad_us_dev || !grad_xw_dev) return fail(c, PS_EINVAL, "ps_mask_nodes_vjp: null argument");
+    if (!c->has_last_mask)
+        return fail(c, PS_ESTATE, "ps_mask_nodes_vjp: the current mask did not come from ps_set_mask_from_nodes");
+    DeviceGuard dg(c->device);
+    const MaskArgs& a = c->last_mask;
+    MaskWs m = mask_ws_split(c->mask_ws, c->p.n);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->gX, 0, (size_t)a.n_nodes * 3 * sizeof(double), c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ps_mask_nodes_vjp");
+    if (a.profile == PS_MASK_TANH) {
+        if (c->fp64) k_mask_vjp_dense<double><<<2432, 128, 0, c->stream>>>(m, a, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
+        else k_mask_vjp_dense<float><<<2432, 128, 0, c->stream>>>(m, a, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
+    } else {
+        if (c->fp64) k_mask_vjp_list<double><<<1216, 256, 0, c->stream>>>(m, a, c->mask_par, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
+        else k_mask_vjp_list<float><<<1216, 256, 0, c->stream>>>(m, a, c->mask_par, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
+    }
+    k_vjp_to_wing<<<(a.n_nodes + 127) / 128, 128, 0, c->stream>>>(a, c->gX, grad_xw_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ps_mask_nodes_vjp");
     return PS_OK;
 }
 

@@ -44,6 +44,10 @@ struct Ops {
     cudaError_t (*step)(const KP&, const Bufs&, int first, cudaStream_t, cudaEvent_t* ev);
     cudaError_t (*set_velocity)(const KP&, const Bufs&, const void* u, cudaStream_t);
     cudaError_t (*get_velocity)(const KP&, const Bufs&, void* u, cudaStream_t);
+    // generic 3-field transforms between compact spectral arrays (3 x
+    // [ky][kx][kz]) and physical arrays (3 x n^3); A, B are used as scratch
+    cudaError_t (*inv3)(const KP&, const Bufs&, const void* spec, void* phys, cudaStream_t);
+    cudaError_t (*fwd3)(const KP&, const Bufs&, const void* phys, void* spec, cudaStream_t);
 };
 
 template <typename T, int N> struct Engine {
@@ -104,6 +108,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
+        if ((e = attr(k_xfwd<T, N, 2>, sm_x5))) return e;
         int occ = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, N>, thr_zp, sm_zp))) return e;
         if (occ < 1) occ = 1;
@@ -175,6 +180,23 @@ template <typename T, int N> struct Engine {
         return cudaGetLastError();
     }
 
+    static cudaError_t inv3(const KP& kp, const Bufs& b, const void* spec, void* phys, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)spec, (C2*)b.A, tw);
+        k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
+        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)phys, tw);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t fwd3(const KP& kp, const Bufs& b, const void* phys, void* spec, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)phys, (C2*)b.B, tw);
+        k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
+        k_xfwd<T, N, 2><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)spec, nullptr,
+                                                                 (const T*)b.Ex, (const T*)b.Ez, 0, tw);
+        return cudaGetLastError();
+    }
+
     static Ops ops() {
         Ops o;
         o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
@@ -185,6 +207,8 @@ template <typename T, int N> struct Engine {
         o.step = &step;
         o.set_velocity = &set_velocity;
         o.get_velocity = &get_velocity;
+        o.inv3 = &inv3;
+        o.fwd3 = &fwd3;
         return o;
     }
 };

@@ -537,7 +537,8 @@ k_yfwd(KP kp, const cplx<T>* __restrict__ B, cplx<T>* __restrict__ A, const cplx
 
 // ---------------------------------------------------------------- pass 5
 // MODE 0: time step (Euler if first != 0, else AB2); MODE 1: set velocity
-// (project with the mean kept, history cleared).
+// (project with the mean kept, history cleared); MODE 2: plain truncated
+// forward transform (times 1/n^3) into U, H untouched.
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(Geo<T, N>::C5 * Geo<T, N>::G)
 k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H,
@@ -589,6 +590,11 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
         const T k2 = kx * kx + ky * ky + kz * kz;
         const bool zero = (mx == 0 && cy == 0 && czz == 0);
+        const size_t o = ((size_t)cy * K + cx) * Kzp + czz;
+        if constexpr (MODE == 2) {   // plain truncated forward transform into U
+            U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
+            continue;
+        }
         if (!zero) {
             const T ik2 = (T)1 / k2;
             const T dr = (kx * n0.x + ky * n1.x + kz * n2.x) * ik2;
@@ -599,7 +605,6 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         } else if (MODE == 0 && !kp.mean_free) {
             n0 = n1 = n2 = cmk<C2>((T)0, (T)0);
         }
-        const size_t o = ((size_t)cy * K + cx) * Kzp + czz;
         if constexpr (MODE == 1) {
             U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
             const C2 z = cmk<C2>((T)0, (T)0);

@@ -14,13 +14,14 @@ _MEAN = {"fixed": B.PS_MEAN_FIXED, "free": B.PS_MEAN_FREE}
 
 
 def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                tw=None, h=None, x0=None):
+                tw=None, h=None, x0=None, with_adjoint=False):
     dx = L / n
     p = B.PsParams()
     p.n = int(n)
     p.precision = _PREC[precision]
     p.mask_profile = _PROFILE[mask_profile]
     p.mean_mode = _MEAN[mean_mode]
+    p.with_adjoint = 1 if with_adjoint else 0
     p.L, p.nu, p.eta, p.dt = float(L), float(nu), float(eta), float(dt)
     p.tw = float(2.0 * dx if tw is None else tw)
     p.h = float(1.5 * dx if h is None else h)
@@ -34,11 +35,11 @@ class Solver:
     """One penalized pseudo-spectral solver on one CUDA device."""
 
     def __init__(self, n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                 tw=None, h=None, x0=None, device=None, stream=None):
+                 tw=None, h=None, x0=None, device=None, stream=None, with_adjoint=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libps needs a CUDA device")
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0)
+        self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0, with_adjoint)
         self.n = int(n)
         self.L = float(L)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -110,6 +111,21 @@ class Solver:
 
     def diagnostics(self):
         return B.ps_diagnostics(self.ctx)
+
+    def adjoint_reset(self):
+        B.ps_adjoint_reset(self.ctx)
+
+    def adjoint_step(self, dJdF, dJdM, first, grad_chi, grad_us):
+        """Reverse one step (see include/ps.h); grad_chi, grad_us are overwritten."""
+        B.ps_adjoint_step(self.ctx, dJdF, dJdM, first, self._field(grad_chi, 1, "grad_chi"),
+                          self._field(grad_us, 3, "grad_us"))
+
+    def mask_nodes_vjp(self, grad_chi, grad_us, grad_xw):
+        """Add dJ/dx^(w) of the last rasterised wing to grad_xw (n_nodes x 3 float64)."""
+        if grad_xw.dtype != torch.float64 or grad_xw.device != self.device or not grad_xw.is_contiguous():
+            raise ValueError("grad_xw must be a contiguous float64 tensor on %s" % self.device)
+        B.ps_mask_nodes_vjp(self.ctx, self._field(grad_chi, 1, "grad_chi"), self._field(grad_us, 3, "grad_us"),
+                            grad_xw.data_ptr())
 
     def timing(self, on=True):
         B.ps_timing_enable(self.ctx, on)
