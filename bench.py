@@ -112,6 +112,28 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` at grid n, scaled from the ncu figure
+    in profiles/traffic.txt by the grid points; None if the kernel sources
+    changed since the counters were taken, or no figure exists."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split(None, 1)
+                kv[k] = v.strip()
+    except OSError:
+        return None
+    src = b"".join(open(os.path.join(ROOT, "paper_2002_08642_gb300", "csrc", f), "rb").read()
+                   for f in ("ps_kernels.cuh", "ps_fft.cuh", "ps_async.cuh"))
+    if kv.get("kernel") != kernel or kv.get("sources_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return float(kv["dram_bytes"]) * (n / float(kv["measured_n"])) ** 3
+
+
 def wing_inputs(cfg, steps):
     from paper_2002_08642_gb300 import inputs
 
@@ -194,11 +216,8 @@ def run_ours(args, cfg):
     total = args.warmup + args.steps
     tri, seq = wing_inputs(cfg, total + args.steps)
     g = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision=cfg["precision"], device=dev)
-    u0 = inputs.random_field(n, L, seed=1234 + rank) if n <= 256 else None
-    if u0 is None:
-        u = torch.zeros((3, n, n, n), dtype=g.dtype, device=dev)
-    else:
-        u = torch.from_numpy(u0).to(dev, g.dtype)
+    # the revolving-wing configurations start from rest (u^0 = 0)
+    u = torch.zeros((3, n, n, n), dtype=g.dtype, device=dev)
     g.set_velocity(u)
     del u
     tri_d = torch.from_numpy(tri).to(dev, torch.int32)
@@ -284,7 +303,7 @@ def run_ours(args, cfg):
                    "precision": cfg["precision"], "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": src, "traffic": None,
+                     "frac": achieved / peak, "peak_source": src, "traffic": measured_traffic(top, n),
                      "algorithmic_bytes_per_launch": ab[top]},
         "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                           "achieved_GBs": step_bytes / (ms / args.steps / 1e3) / 1e9},
@@ -295,9 +314,9 @@ def run_ours(args, cfg):
     }
     if clk:
         out["clocks"] = clk
+    del g
+    torch.cuda.empty_cache()
     if args.fp64 and world == 1:
-        del g
-        torch.cuda.empty_cache()
         g64 = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision="fp64", device=dev)
         g64.set_velocity(torch.zeros((3, n, n, n), dtype=torch.float64, device=dev))
         k64 = max(2, args.steps // 4)
@@ -315,6 +334,37 @@ def run_ours(args, cfg):
         v64 = n ** 3 * k64 / (ms64 / 1e3) / 1e6
         out["fp64_step"] = {"value": v64, "unit": "Mpts*steps/s", "steps": k64, "ms_per_step": ms64 / k64,
                             "fp32_speedup": value / v64}
+        del g64
+        torch.cuda.empty_cache()
+    if args.adjoint and world == 1:
+        # adjoint step throughput at 512^3 (FP32): one reversed step per call,
+        # on the state and mask reached by a few forward steps
+        na = 512
+        ga = Solver(na, L, cfg["nu"], cfg["eta"], cfg["dt"], precision="fp32", device=dev, with_adjoint=True)
+        ga.set_velocity(torch.zeros((3, na, na, na), dtype=torch.float32, device=dev))
+        ga.set_mask_from_nodes(xw_d[0], vw_d[0], tri_d, frames[0])
+        ga.step(2)
+        gc = torch.empty((na, na, na), dtype=torch.float32, device=dev)
+        gs = torch.empty((3, na, na, na), dtype=torch.float32, device=dev)
+        gx = torch.zeros_like(xw_d[0])
+        ga.adjoint_reset()
+        for _ in range(2):
+            ga.adjoint_step((0, 0, 1.0), (0, 0, 0), False, gc, gs)
+            ga.mask_nodes_vjp(gc, gs, gx)
+        ka = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ka):
+            ga.adjoint_step((0, 0, 1.0), (0, 0, 0), False, gc, gs)
+            ga.mask_nodes_vjp(gc, gs, gx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msa = e0.elapsed_time(e1)
+        out["adjoint_step"] = {"value": na ** 3 * ka / (msa / 1e3) / 1e6, "unit": "Mpts*steps/s", "n": na,
+                               "precision": "fp32", "steps": ka, "ms_per_step": msa / ka,
+                               "note": "reversed step + rasteriser VJP, excluding the checkpoint recompute"}
+        del ga
+        torch.cuda.empty_cache()
     if rank == 0 and args.cpu_baseline:
         r, k, cn = cpu_oracle_rate(cfg)
         out["cpu_baseline"] = {"value": r, "unit": "Mpts*steps/s", "cores": 1, "kind": "oracle",
@@ -335,6 +385,7 @@ def main():
     ap.add_argument("--workload", default="wing768", choices=sorted(WORKLOADS))
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
