@@ -402,18 +402,14 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         __syncthreads();
         double fm[6] = {0, 0, 0, 0, 0, 0};
         bool touched = false;
-        for (int idx = threadIdx.x; idx < LZ * N; idx += blockDim.x) {
-            const int l = idx / N, z = idx % N;
+        // n = u x w - (chi/eta)(u - us) of line l at z; forces in double
+        auto nonlinear = [&](int l, int z, int a, T& nx, T& ny, T& nz) {
             const long lid = (long)b * LZ + l;
-            const int a = zad(z);
-            C2* t0 = tile(l, 0);
-            C2* t1 = tile(l, 1);
-            C2* t2 = tile(l, 2);
-            const C2 z0 = t0[a], z1 = t1[a], z2 = t2[a];
+            const C2 z0 = tile(l, 0)[a], z1 = tile(l, 1)[a], z2 = tile(l, 2)[a];
             const T ux = z0.x, uy = z0.y, uz = z1.x, wx = z1.y, wy = z2.x, wz = z2.y;
-            T nx = uy * wz - uz * wy;
-            T ny = uz * wx - ux * wz;
-            T nz = ux * wy - uy * wx;
+            nx = uy * wz - uz * wy;
+            ny = uz * wx - ux * wz;
+            nz = ux * wy - uy * wx;
             if (flag[lid] != 0) {
                 const size_t po = (size_t)lid * N + z;
                 const T c = chi[po];
@@ -438,9 +434,19 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                     touched = true;
                 }
             }
-            // this thread alone reads and writes these slots of line l
-            t0[a] = cmk<C2>(nx, ny);
-            reinterpret_cast<T*>(t2 + a)[0] = nz;
+        };
+        // lines 2m and 2m+1 together: (n_x + i n_y) of each in place of
+        // (u_x + i u_y), and (n_z[2m] + i n_z[2m+1]) in place of line 2m's
+        // (u_z + i w_x); this thread alone reads and writes these slots
+        for (int idx = threadIdx.x; idx < (LZ / 2) * N; idx += blockDim.x) {
+            const int l = 2 * (idx / N), z = idx % N;
+            const int a = zad(z);
+            T nx0, ny0, nz0, nx1, ny1, nz1;
+            nonlinear(l, z, a, nx0, ny0, nz0);
+            nonlinear(l + 1, z, a, nx1, ny1, nz1);
+            tile(l, 0)[a] = cmk<C2>(nx0, ny0);
+            tile(l + 1, 0)[a] = cmk<C2>(nx1, ny1);
+            tile(l, 1)[a] = cmk<C2>(nz0, nz1);
         }
         // this batch's force sums: warp tree, then compensated into the warp slot
         if (__any_sync(0xffffffffu, touched)) {
@@ -455,12 +461,6 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                     w[2 * i + 1] = a.c;
                 }
             }
-        }
-        __syncthreads();
-        // n_z of lines 2m and 2m+1 share one complex line: (n_z[2m] + i n_z[2m+1])
-        for (int idx = threadIdx.x; idx < (LZ / 2) * N; idx += blockDim.x) {
-            const int l = 2 * (idx / N), a = zad(idx % N);
-            tile(l, 1)[a] = cmk<C2>(tile(l, 2)[a].x, tile(l + 1, 2)[a].x);
         }
         __syncthreads();
         {
