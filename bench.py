@@ -103,6 +103,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, world):
+    """Max of a per-rank float over the process group (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -257,10 +270,7 @@ def run_ours(args, cfg):
     g.timing(False)
     clk = clocks.stop()
     F, M = g.forces()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     value = n ** 3 * args.steps * world / (ms / 1e3) / 1e6
 
     # ---- end to end through the public API with host buffers

@@ -9,7 +9,8 @@
 //          x/y index c in [0, K) <-> mode m = c (c <= mmax) or c - K,
 //          z index c in [0, Kz) <-> mode m = c; K = 2 mmax + 1, Kz = mmax + 1,
 //          mmax = (n - 1) / 3, Kzp = Kz rounded up to the tile width.
-//   A      after the x transform: nf x [n][K][Kzp]   (x physical, y/z spectral)
+//   A      after the x transform: nf x [n][K][Kzp]   (x physical, y/z spectral;
+//          also the y-forward output read by the x-forward pass)
 //   B      after the y transform: nf x [n][n][Kzp]   (x/y physical, z spectral)
 //   chi    n^3 real, us 3 x n^3 real, line flag [n][n] (1 if the z line
 //          touches chi > 0)
@@ -17,7 +18,11 @@
 // it: the x pass reads K of n rows, the y pass K of n rows, and the z pass
 // Kz of n/2+1 entries per line.
 //
-// Pass order of a step (P = Leray projection, E = exp(-nu |k|^2 dt)):
+// Pass order of a step (P = Leray projection, E = exp(-nu |k|^2 dt)); the
+// step uses the TMA-staged kernels k_xinv_tma, k_yinv_tma, k_zpass,
+// k_yfwd_tma, k_xfwd_tma; the plain kernels k_xinv/k_yinv/k_yfwd/k_xfwd and
+// the physical <-> z-spectral kernels serve ps_set/get_velocity and the
+// adjoint's generic transforms:
 //   1 x-inverse of u_hat and omega_hat = i k x u_hat (curl fused)    U -> A (6)
 //   2 y-inverse                                                      A -> B (6)
 //   3 z c2r, n = u x omega - (chi/eta)(u - u_s), force/moment partial
@@ -59,6 +64,7 @@
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
 #endif
+
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
 
