@@ -186,9 +186,11 @@ ps_status ps_mask_nodes_vjp(ps_ctx* ctx, const void* grad_chi_dev, const void* g
 /* Per-pass device timing with CUDA events on the context's stream.
  * ps_timing_enable(ctx, 1) resets the accumulators and records events around
  * each pass of every following ps_step (and around ps_set_mask_from_nodes)
- * for up to 1024 calls; 0 stops recording. ps_timing_read synchronises and
+ * for up to 256 steps; 0 stops recording. ps_timing_read synchronises and
  * writes, for each of *count passes (named by ps_timing_name(i)), the summed
- * milliseconds and the number of timed launches. With ms or launches NULL or
+ * milliseconds and the number of timed steps (a pass split into x slabs that
+ * run on two streams counts the sum of its slab kernels' times, each measured
+ * on its own stream, once per step). With ms or launches NULL or
  * cap too small it only sets *count. */
 ps_status ps_timing_enable(ps_ctx* ctx, int32_t on);
 ps_status ps_timing_read(ps_ctx* ctx, double* ms, int64_t* launches, int32_t cap, int32_t* count);

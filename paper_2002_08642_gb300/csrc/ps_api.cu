@@ -27,6 +27,10 @@ struct ps_ctx {
     int fp64;
     const Ops* ops;
     int zblocks;        // force partials written by the z pass
+    int nslab;          // slabs of the y/z/y pipeline
+    cudaStream_t aux[2];
+    cudaEvent_t sev[3];
+    bool aux_ok;
     KP kp;
     Bufs b;
     size_t elem;        // bytes of one real
@@ -40,6 +44,7 @@ struct ps_ctx {
     CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
     CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
+    CUtensorMap tmBo;         // B in y-forward boxes of the slab pipeline
     // adjoint (with_adjoint): lam, mu, G, W, Ub, Wb spectral; u, w, nb physical
     void* adj_spec[6];
     void* adj_phys[3];
@@ -50,13 +55,13 @@ struct ps_ctx {
     int has_velocity;
     // per-pass timing: a ring of events, kTimingRing steps deep
     bool timing;
-    std::vector<cudaEvent_t> tev_step;   // kTimingRing x 6
+    std::vector<cudaEvent_t> tev_step;   // kTimingRing x kEvPerStep
     std::vector<cudaEvent_t> tev_mask;   // kTimingRing x 2
     long t_steps, t_masks;
     std::string err;
 };
 
-static const int kTimingRing = 1024;
+static const int kTimingRing = 256;
 static const char* kPassNames[] = {"x_inverse_curl", "y_inverse", "z_c2r_nonlinear_r2c", "y_forward",
                                    "x_forward_project_ab2", "rasterise"};
 
@@ -487,7 +492,17 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm < 1) nsm = 1;
-    cudaError_t e = ops->prepare(nsm, &c->zblocks);
+    cudaError_t e = ops->prepare(nsm, &c->zblocks, &c->nslab);
+    if (e == cudaSuccess && c->nslab > 1) {
+        if ((e = cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking)) == cudaSuccess &&
+            (e = cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking)) == cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&c->sev[0], cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&c->sev[1], cudaEventDisableTiming)) == cudaSuccess &&
+            (e = cudaEventCreateWithFlags(&c->sev[2], cudaEventDisableTiming)) == cudaSuccess)
+            c->aux_ok = true;
+        for (int i = 0; i < 2; ++i) c->b.aux[i] = c->aux[i];
+        for (int i = 0; i < 3; ++i) c->b.sev[i] = c->sev[i];
+    }
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
         if (!encode_rows(&c->tmA, c->b.A, c->fp64, (size_t)6 * n * Kk, kp.Kzp, ops->cy2, ops->br2) ||
@@ -495,7 +510,8 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
             !encode_rows(&c->tmU, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2) ||
             !encode_planes(&c->tmA5, c->b.A, c->fp64, kp.Kzp, (size_t)Kk, (size_t)6 * n, ops->cx5, ops->br4) ||
             !encode_rows(&c->tmUp, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
-            !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2)) {
+            !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
+            !encode_rows(&c->tmBo, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4o, ops->br4)) {
             delete c;
             return PS_ECUDA;
         }
@@ -505,6 +521,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         c->b.tmA5 = &c->tmA5;
         c->b.tmUp = &c->tmUp;
         c->b.tmHp = &c->tmHp;
+        c->b.tmBo = &c->tmBo;
     }
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;
@@ -525,6 +542,12 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
 ps_status ps_destroy(ps_ctx* c) {
     if (!c) return PS_EINVAL;
     for (cudaEvent_t ev : c->tev_step) cudaEventDestroy(ev);
+    if (c->aux_ok) {
+        cudaStreamSynchronize(c->aux[0]);
+        cudaStreamSynchronize(c->aux[1]);
+        for (int i = 0; i < 2; ++i) cudaStreamDestroy(c->aux[i]);
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(c->sev[i]);
+    }
     for (cudaEvent_t ev : c->tev_mask) cudaEventDestroy(ev);
     delete c;
     return PS_OK;
@@ -633,7 +656,7 @@ ps_status ps_step(ps_ctx* c, int32_t nsteps) {
     DeviceGuard dg(c->device);
     for (int i = 0; i < nsteps; ++i) {
         cudaEvent_t* ev = nullptr;
-        if (c->timing) ev = &c->tev_step[(size_t)(c->t_steps++ % kTimingRing) * 6];
+        if (c->timing) ev = &c->tev_step[(size_t)(c->t_steps++ % kTimingRing) * kEvPerStep];
         cudaError_t e = c->ops->step(c->kp, c->b, c->nstep == 0, c->stream, ev);
         if (e != cudaSuccess) return cuda_fail(c, e, "ps_step");
         c->nstep++;
@@ -775,7 +798,7 @@ ps_status ps_timing_enable(ps_ctx* c, int32_t on) {
     if (!c) return PS_EINVAL;
     DeviceGuard dg(c->device);
     if (on && c->tev_step.empty()) {
-        c->tev_step.resize((size_t)kTimingRing * 6);
+        c->tev_step.resize((size_t)kTimingRing * kEvPerStep);
         c->tev_mask.resize((size_t)kTimingRing * 2);
         for (cudaEvent_t& ev : c->tev_step)
             if (cudaEventCreate(&ev) != cudaSuccess) return fail(c, PS_ECUDA, "ps_timing_enable: cudaEventCreate");
@@ -798,14 +821,23 @@ ps_status ps_timing_read(ps_ctx* c, double* ms, int64_t* launches, int32_t cap, 
     if (s != PS_OK) return s;
     for (int i = 0; i < np; ++i) { ms[i] = 0.0; launches[i] = 0; }
     const long ns = c->t_steps < kTimingRing ? c->t_steps : kTimingRing;
+    auto el = [&](cudaEvent_t a0, cudaEvent_t a1, double* acc) -> bool {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, a0, a1) != cudaSuccess) return false;
+        *acc += t;
+        return true;
+    };
+    const int S = c->nslab > 1 ? c->nslab : 1;
     for (long k = 0; k < ns; ++k) {
-        cudaEvent_t* ev = &c->tev_step[(size_t)k * 6];
-        for (int i = 0; i < 5; ++i) {
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) != cudaSuccess) return fail(c, PS_ECUDA, "ps_timing_read");
-            ms[i] += t;
-            launches[i] += 1;
+        cudaEvent_t* ev = &c->tev_step[(size_t)k * kEvPerStep];
+        bool ok = el(ev[0], ev[1], &ms[0]);
+        for (int sl = 0; sl < S && ok; ++sl) {
+            cudaEvent_t* e = ev + 2 + 6 * sl;
+            ok = el(e[0], e[1], &ms[1]) && el(e[2], e[3], &ms[2]) && el(e[4], e[5], &ms[3]);
         }
+        ok = ok && el(ev[2 + 6 * kMaxSlabs], ev[3 + 6 * kMaxSlabs], &ms[4]);
+        if (!ok) return fail(c, PS_ECUDA, "ps_timing_read");
+        for (int i = 0; i < 5; ++i) launches[i] += 1;
     }
     const long nm = c->t_masks < kTimingRing ? c->t_masks : kTimingRing;
     for (long k = 0; k < nm; ++k) {

@@ -64,6 +64,9 @@
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
 #endif
+#ifndef PS_Y4O_SMEM_KB
+#define PS_Y4O_SMEM_KB 120
+#endif
 
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
@@ -76,6 +79,8 @@ struct KP {
     double dt, inv_eta, invn3, dx, half_L3;
     double x0[3];
     int mean_free;
+    int xs0, xsn;     // x planes [xs0, xs0 + xsn) handled by the y and z passes
+    int part_off;     // first force-partial slot of this z-pass launch
 };
 
 __device__ __forceinline__ int mode_of(int q, int n) { return q < n / 2 ? q : q - n; }
@@ -185,6 +190,8 @@ template <typename T, int N> struct Geo {
     static constexpr int CY4 = pick_c(4, PS_Y4_SMEM_KB, 16);
     static constexpr int CX1 = pick_c(2, PS_X1_SMEM_KB, 16);
     static constexpr int CX5 = pick_c(5, PS_X5_SMEM_KB, 128 / 16);
+    // y-forward tile when it shares SMs with the z pass (slab pipeline)
+    static constexpr int CY4O = pick_c(4, PS_Y4O_SMEM_KB, 16);
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
 
@@ -305,7 +312,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
-    constexpr int nbatch = N * N / LZ;
+    const int b0 = kp.xs0 * N / LZ, b1 = (kp.xs0 + kp.xsn) * N / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][6][LZ][KZP]
@@ -339,14 +346,14 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         for (int f = 0; f < 6; ++f)
             bulk_g2s(stage + (size_t)(buf * 6 + f) * LZ * KZP, B + f * BS + (size_t)b * LZ * KZP, fbytes, &bar[buf]);
     };
-    if (threadIdx.x == 0 && (int)blockIdx.x < nbatch) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0 && b0 + (int)blockIdx.x < b1) issue(b0 + blockIdx.x, 0);
 
     const size_t N3 = (size_t)N * N * N;
     const T inv_eta = (T)kp.inv_eta;
     int it = 0;
-    for (int b = blockIdx.x; b < nbatch; b += gridDim.x, ++it) {
+    for (int b = b0 + blockIdx.x; b < b1; b += gridDim.x, ++it) {
         const int buf = it & 1;
-        const bool more = b + (int)gridDim.x < nbatch;
+        const bool more = b + (int)gridDim.x < b1;
         if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
         const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
         if (__syncthreads_or(!ok)) {
@@ -503,7 +510,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             a.add(wacc[w][2 * threadIdx.x]);
             a.add(wacc[w][2 * threadIdx.x + 1]);
         }
-        partial[(size_t)blockIdx.x * 6 + threadIdx.x] = a.val();
+        partial[(size_t)(kp.part_off + blockIdx.x) * 6 + threadIdx.x] = a.val();
     }
 }
 
@@ -652,7 +659,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     constexpr int CT = GE::CY2, G = GE::G, K = GE::K, KZP = GE::KZP;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
     constexpr int NTZ = KZP / CT;
-    constexpr int NITEM = N * NTZ * 6;
+    const int NITEM = kp.xsn * NTZ * 6;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -674,7 +681,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     load_tw(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int i, int buf) {  // one thread
-        const int f = i % 6, t = i / 6, x = t / NTZ, czt = t % NTZ;
+        const int f = i % 6, t = i / 6, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -695,7 +702,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             }
             break;
         }
-        const int f = i % 6, t = i / 6, x = t / NTZ, czt = t % NTZ;
+        const int f = i % 6, t = i / 6, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         const C2* Sb = S + (size_t)buf * RS * CT;
@@ -715,17 +722,17 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 
 // pass 4: y-forward of the three fields, B (all y rows) -> A (kept ky rows).
 // tm: B as a 2-D array of 6 n n rows of 2 Kzp reals.
-template <typename T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::CY4 * Geo<T, N>::G)
+template <typename T, int N, int CTV>
+__global__ void __launch_bounds__(CTV * Geo<T, N>::G)
 k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
-    constexpr int CT = GE::CY4, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int CT = CTV, G = GE::G, K = GE::K, KZP = GE::KZP;
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "y-forward staging must be contiguous in y");
     constexpr int NTZ = KZP / CT;
-    constexpr int NITEM = N * NTZ * 3;
+    const int NITEM = kp.xsn * NTZ * 3;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -746,7 +753,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     load_tw(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int i, int buf) {  // one thread
-        const int f = i % 3, t = i / 3, x = t / NTZ, czt = t % NTZ;
+        const int f = i % 3, t = i / 3, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -766,7 +773,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             }
             break;
         }
-        const int f = i % 3, t = i / 3, x = t / NTZ, czt = t % NTZ;
+        const int f = i % 3, t = i / 3, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         C2* Sb = S + (size_t)buf * RS * CT;
