@@ -96,7 +96,7 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->chi = take(n3 * er);
     L->us = take(3 * n3 * er);
     L->flag = take((size_t)n * n);
-    L->tw = take((size_t)n * ec);
+    L->tw = take((size_t)3 * n * ec);   // n-line table, then (n = 3M) the M-line table at n and e^{2 pi i b q/n} at 2n
     L->Ex = take((size_t)K * er);
     L->Ez = take((size_t)Kz * er);
     const size_t nparts = (size_t)n * n + 4096;
@@ -210,15 +210,29 @@ void host_tables(const ps_params* p, std::vector<unsigned char>& tw, std::vector
                  std::vector<unsigned char>& ez) {
     using C2 = cplx<T>;
     const int n = p->n, mm = mmax_of(n), K = 2 * mm + 1, Kz = mm + 1;
-    const int S = n_stages(n);
-    std::vector<C2> t((size_t)(tw_count(n) > 0 ? tw_count(n) : 1));
-    for (int s = 1; s < S; ++s) {
-        const int r = radix_at(n, s), Ls = ls_at(n, s), o = tw_offset(n, s);
-        for (int tt = 1; tt < r; ++tt)
-            for (int k = 0; k < Ls; ++k) {
+    std::vector<C2> t((size_t)3 * n, cmk<C2>((T)0, (T)0));
+    // stage twiddles of a length-m line at offset `base`
+    auto line_table = [&](int m, size_t base) {
+        const int S = n_stages(m);
+        for (int s = 1; s < S; ++s) {
+            const int r = radix_at(m, s), Ls = ls_at(m, s), o = tw_offset(m, s);
+            for (int tt = 1; tt < r; ++tt)
+                for (int k = 0; k < Ls; ++k) {
+                    double c, sn;
+                    unit_root((long)tt * k, (long)Ls * r, &c, &sn);
+                    t[base + o + (tt - 1) * Ls + k] = cmk<C2>((T)c, (T)sn);
+                }
+        }
+    };
+    line_table(n, 0);
+    if (n % 3 == 0) {
+        const int M = n / 3;
+        line_table(M, (size_t)n);
+        for (int b = 1; b <= 2; ++b)
+            for (int q = 0; q < M; ++q) {
                 double c, sn;
-                unit_root((long)tt * k, (long)Ls * r, &c, &sn);
-                t[o + (tt - 1) * Ls + k] = cmk<C2>((T)c, (T)sn);
+                unit_root((long)b * q, (long)n, &c, &sn);
+                t[(size_t)2 * n + (b - 1) * M + q] = cmk<C2>((T)c, (T)sn);
             }
     }
     tw.assign((unsigned char*)t.data(), (unsigned char*)(t.data() + t.size()));

@@ -42,11 +42,9 @@
 #ifndef PS_ZP_MINB
 #define PS_ZP_MINB 0   // 0: 3 blocks per SM up to n = 256, 2 above
 #endif
-// 1: the first inverse stage reads the staged spectral lines directly
-// (two-for-one combination in registers); 0: a separate pass builds the
-// complex lines in the tiles first
-#ifndef PS_ZP_DIRECT
-#define PS_ZP_DIRECT 1
+// 1: z lines of n = 3M done as three length-M transforms (see k_zpass)
+#ifndef PS_Z3
+#define PS_Z3 1
 #endif
 // tile width of the TMA-staged y passes (0 = automatic)
 #ifndef PS_TY_C
@@ -304,6 +302,16 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // forward transforms of (n_x + i n_y) per line and of (n_z[l] + i n_z[l+1])
 // per line pair; the result, truncated to kz < Kz, overwrites fields 0..2 of
 // B (only this batch's lines, whose input is already in shared memory).
+//
+// For n = 3M the 2/3 truncation leaves the middle third of every z spectrum
+// empty (Kz = M), so a length-n line is done as three length-M transforms:
+// inverse  z[3a + b] = sum_q' e^{2 pi i a q'/M} Y_b[q'],
+//          Y_b[q'] = e^{2 pi i b q'/n} (Z[q'] + e^{2 pi i 2b/3} Z[q' + 2M]),
+// forward  Z[k'] = sum_b e^{-2 pi i b k'/n} F_b[k'],
+//          Z[2M + k'] = sum_b e^{-2 pi i 2b/3} e^{-2 pi i b k'/n} F_b[k'],
+// F_b the forward length-M transform of z[3a + b]; sub-line b of a tile
+// holds z[3a + b] at position b M + a, so the pointwise phase reads and
+// writes in place and no reordering pass is needed.
 template <typename T, int N>
 __global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
@@ -312,6 +320,11 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
+    constexpr bool Z3 = (N % 3 == 0) && (PS_Z3 != 0);
+    constexpr int M = Z3 ? N / 3 : N;
+    constexpr int GM = LineFFT<T, M, 1>::G;        // threads per sub-line
+    static_assert(!Z3 || G == 3 * GM, "three sub-lines per line group");
+    constexpr int TWM = Z3 ? (tw_count(M) > 0 ? tw_count(M) : 1) : 0;
     const int b0 = kp.xs0 * N / LZ, b1 = (kp.xs0 + kp.xsn) * N / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -335,7 +348,13 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    load_tw(tw, twg, GE::tw_n);
+    C2* tw3 = tw + TWM;   // n = 3M: e^{+2 pi i b q'/n}, b = 1, 2
+    if constexpr (Z3) {
+        if constexpr (tw_count(M) > 0) load_tw(tw, twg + N, tw_count(M));
+        load_tw(tw3, twg + 2 * N, 2 * M);
+    } else {
+        load_tw(tw, twg, GE::tw_n);
+    }
     for (int i = threadIdx.x; i < 32 * 12; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
     __syncthreads();
     auto issue = [&](int b, int buf) {  // one thread
@@ -365,8 +384,31 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             break;
         }
         const C2* st = stage + (size_t)buf * 6 * LZ * KZP;
-#if PS_ZP_DIRECT
-        {
+        if constexpr (Z3) {
+            const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
+            const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
+            const int sub = g / GM, gm = g % GM;
+            const int tbase = (int)(tile(pl, pr) - tiles) ;
+            auto addr = [&](int p) { return tbase + zad(sub * M + p); };
+            const T h3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
+            auto load = [&](int q) -> C2 {
+                C2 a = fa[q], c = fb[q];
+                if (q == 0) { a.y = 0; c.y = 0; }
+                C2 v = cmk<C2>(a.x - c.y, a.y + c.x);                      // Z[q]
+                C2 w = cmk<C2>((T)0, (T)0);
+                if (q > 0) {
+                    const C2 a2 = fa[M - q], c2 = fb[M - q];
+                    w = cmk<C2>(a2.x + c2.y, c2.x - a2.y);                 // Z[q + 2M]
+                }
+                if (sub == 0) return cadd(v, w);
+                // e^{2 pi i 2 sub / 3}: sub 1 -> (-1/2, -h), sub 2 -> (-1/2, +h)
+                const T sg = sub == 1 ? -h3 : h3;
+                v = cmk<C2>(v.x - (T)0.5 * w.x - sg * w.y, v.y - (T)0.5 * w.y + sg * w.x);
+                return cmul(v, tw3[(sub - 1) * M + q]);
+            };
+            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
+            LineFFT<T, M, 1>::template run<false>(tiles, tw, addr, gm, load, store);
+        } else {
             const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
             const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
             const int tbase = (int)(tile(pl, pr) - tiles);
@@ -386,32 +428,6 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
             LineFFT<T, N, 1>::template run<false>(tiles, tw, addr, g, load, store);
         }
-#else
-        // spectral lines -> two-for-one complex lines in the tiles
-        for (int idx = threadIdx.x; idx < 3 * LZ * N; idx += blockDim.x) {
-            const int q = idx % N, lp = idx / N, l = lp / 3, p = lp % 3;
-            const C2* fa = st + (size_t)((2 * p) * LZ + l) * KZP;
-            const C2* fb = st + (size_t)((2 * p + 1) * LZ + l) * KZP;
-            C2 v = cmk<C2>((T)0, (T)0);
-            if (q < Kz) {
-                C2 a = fa[q], c = fb[q];
-                if (q == 0) { a.y = 0; c.y = 0; }
-                v = cmk<C2>(a.x - c.y, a.y + c.x);                 // A + i B
-            } else if (q > N - Kz) {
-                const C2 a = fa[N - q], c = fb[N - q];
-                v = cmk<C2>(a.x + c.y, c.x - a.y);                 // conj(A) + i conj(B)
-            }
-            tile(l, p)[zad(q)] = v;
-        }
-        __syncthreads();
-        {
-            const int tbase = (int)(tile(pl, pr) - tiles);
-            auto addr = [&](int p) { return tbase + zad(p); };
-            auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
-            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-            LineFFT<T, N, 1>::template run<true>(tiles, tw, addr, g, noload, store);
-        }
-#endif
         __syncthreads();
         double fm[6] = {0, 0, 0, 0, 0, 0};
         bool touched = false;
@@ -452,8 +468,10 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         // (u_x + i u_y), and (n_z[2m] + i n_z[2m+1]) in place of line 2m's
         // (u_z + i w_x); this thread alone reads and writes these slots
         for (int idx = threadIdx.x; idx < (LZ / 2) * N; idx += blockDim.x) {
-            const int l = 2 * (idx / N), z = idx % N;
-            const int a = zad(z);
+            const int l = 2 * (idx / N), r = idx % N;
+            // tile position r holds z = r (n = 3M: z = 3 (r mod M) + r / M)
+            const int z = Z3 ? 3 * (r % M) + r / M : r;
+            const int a = zad(r);
             T nx0, ny0, nz0, nx1, ny1, nz1;
             nonlinear(l, z, a, nx0, ny0, nz0);
             nonlinear(l + 1, z, a, nx1, ny1, nz1);
@@ -480,12 +498,36 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             // forward lines: (l, 0) for every l, (l, 1) for even l; others idle
             const bool active = (pr == 0) || (pr == 1 && (pl & 1) == 0);
             const int tbase = (int)(tile(pl, pr == 2 ? 1 : pr) - tiles);
-            auto addr = [&](int p) { return tbase + zad(p); };
             auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
-            auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
-            LineFFT<T, N, -1>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
+            if constexpr (Z3) {
+                const int sub = g / GM, gm = g % GM;
+                auto addr = [&](int p) { return tbase + zad(sub * M + p); };
+                auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
+                LineFFT<T, M, -1>::template run_masked<true>(tiles, tw, addr, gm, noload, store, active);
+            } else {
+                auto addr = [&](int p) { return tbase + zad(p); };
+                auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
+                LineFFT<T, N, -1>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
+            }
         }
         __syncthreads();
+        if constexpr (Z3) {
+            // radix-3 recombination of the three sub-line spectra, kept modes only
+            const T h3 = (T)0.86602540378443864676;
+            for (int idx = threadIdx.x; idx < (LZ + LZ / 2) * M; idx += blockDim.x) {
+                const int fl2 = idx / M, kq = idx % M;
+                C2* t = fl2 < LZ ? tile(fl2, 0) : tile(2 * (fl2 - LZ), 1);
+                const C2 F0 = t[zad(kq)], F1 = t[zad(M + kq)], F2 = t[zad(2 * M + kq)];
+                const C2 G1 = cmul(F1, cconj(tw3[kq])), G2 = cmul(F2, cconj(tw3[M + kq]));
+                const C2 Zk = cadd(F0, cadd(G1, G2));
+                // e^{-2 pi i 2/3} = (-1/2, +h), e^{-2 pi i 4/3} = (-1/2, -h)
+                const C2 Zm = cmk<C2>(F0.x - (T)0.5 * (G1.x + G2.x) - h3 * (G1.y - G2.y),
+                                      F0.y - (T)0.5 * (G1.y + G2.y) + h3 * (G1.x - G2.x));
+                t[zad(kq)] = Zk;
+                t[zad(2 * M + kq)] = Zm;
+            }
+            __syncthreads();
+        }
         // unpack the two-for-one transforms, keep kz < Kz
         for (int idx = threadIdx.x; idx < LZ * Kz; idx += blockDim.x) {
             const int l = idx / Kz, k = idx % Kz;
