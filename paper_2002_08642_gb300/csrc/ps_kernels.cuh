@@ -203,6 +203,58 @@ __device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
     return raw + ((128u - (a & 127u)) & 127u);
 }
 
+// ----------------------------------------------- n = 3M split of a line
+// With the 2/3 rule and n = 3M, a line's kept modes are q in [0, M) and
+// (2M, 3M): the middle third is empty. The inverse transform then is three
+// length-M transforms, z[3a + b] = sum_q e^{2 pi i a q / M} Y_b[q],
+//   Y_b[q] = e^{2 pi i b q / n} (X[q] + e^{2 pi i 2b/3} X[q + 2M]),
+// and the forward transform's kept outputs come from the length-M
+// transforms F_b of z[3a + b]:
+//   Z[k] = sum_b e^{-2 pi i b k/n} F_b[k],
+//   Z[2M + k] = sum_b e^{-2 pi i 2b/3} e^{-2 pi i b k/n} F_b[k].
+// tw3[(b - 1) M + q] = e^{+2 pi i b q / n} (b = 1, 2).
+// The z pass uses both directions; the TMA x and y passes use the forward
+// one (split3_out). Their inverses keep the length-n transform: the split's
+// two-mode input loads and per-sub-line register sets cost more there than
+// the stage it saves.
+template <typename T, int N> struct Split3 {
+    static constexpr bool on = (N % 3 == 0) && (PS_Z3 != 0);
+    static constexpr int M = on ? N / 3 : N;
+    static constexpr int GM = LineFFT<T, M, 1>::G;                     // threads per sub-line
+    static constexpr int TWM = on ? (tw_count(M) > 0 ? tw_count(M) : 1) : 0;
+    // the block's thread groups split evenly over the three sub-lines, and
+    // the M table plus tw3 fit in the room of the n table (+ 1)
+    static_assert(!on || 3 * GM == LineFFT<T, N, 1>::G, "n = 3M split: group count");
+    static_assert(!on || TWM + 2 * M <= tw_count(N) + 1, "n = 3M split: twiddle room");
+};
+
+// Z[k] and Z[2M + k] from F_0[k], F_1[k], F_2[k].
+template <typename C2>
+__device__ __forceinline__ void split3_out(C2 F0, C2 F1, C2 F2, const C2* tw3, int k, int M, C2& Zk, C2& Zm) {
+    using T = typename real_of<C2>::type;
+    const T h3 = (T)0.86602540378443864676;
+    const C2 G1 = cmul(F1, cconj(tw3[k])), G2 = cmul(F2, cconj(tw3[M + k]));
+    Zk = cadd(F0, cadd(G1, G2));
+    // e^{-2 pi i 2/3} = (-1/2, +h), e^{-2 pi i 4/3} = (-1/2, -h)
+    Zm = cmk<C2>(F0.x - (T)0.5 * (G1.x + G2.x) - h3 * (G1.y - G2.y),
+                 F0.y - (T)0.5 * (G1.y + G2.y) + h3 * (G1.x - G2.x));
+}
+
+// Twiddles into shared memory: the n-line table, or for the n = 3M split
+// the M-line table followed by tw3 (both fit in the n-line table's room).
+template <typename T, int N>
+__device__ __forceinline__ cplx<T>* load_tw_split(cplx<T>* tw, const cplx<T>* twg, int n_tw) {
+    using S3 = Split3<T, N>;
+    if constexpr (S3::on) {
+        for (int i = threadIdx.x; i < tw_count(S3::M); i += blockDim.x) tw[i] = twg[N + i];
+        for (int i = threadIdx.x; i < 2 * S3::M; i += blockDim.x) tw[S3::TWM + i] = twg[2 * N + i];
+        return tw + S3::TWM;
+    } else {
+        for (int i = threadIdx.x; i < n_tw; i += blockDim.x) tw[i] = twg[i];
+        return tw;
+    }
+}
+
 template <typename C2>
 __device__ __forceinline__ void load_tw(C2* s, const C2* g, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = g[i];
@@ -792,7 +844,8 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    load_tw(tw, twg, GE::tw_n);
+    using S3 = Split3<T, N>;
+    const C2* tw3 = load_tw_split<T, N>(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int i, int buf) {  // one thread
         const int f = i % 3, t = i / 3, x = kp.xs0 + t / NTZ, czt = t % NTZ;
@@ -819,13 +872,36 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         C2* Sb = S + (size_t)buf * RS * CT;
-        auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
         auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
-        auto store = [&](int q, C2 v) {
-            const int m = mode_of(q, N);
-            if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * KZP + cz] = v;
-        };
-        LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+        if constexpr (S3::on) {
+            // sub-line b = rows y = 3a + b, transformed in place; then the
+            // kept outputs by the radix-3 recombination
+            constexpr int M = S3::M;
+            const int sub = g / S3::GM, gm = g % S3::GM;
+            auto addr3 = [&](int p) { return (int)(Sb - S) + (3 * p + sub) * CT + col; };
+            auto store = [&](int p, C2 v) { S[addr3(p)] = v; };
+            LineFFT<T, M, -1>::template run<true>(S, tw, addr3, gm, noload, store);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < M * CT; idx += blockDim.x) {
+                const int kq = idx / CT, c = idx % CT;
+                const int czz = czt * CT + c;
+                C2 Zk, Zm;
+                split3_out(Sb[(3 * kq) * CT + c], Sb[(3 * kq + 1) * CT + c], Sb[(3 * kq + 2) * CT + c], tw3, kq, M,
+                           Zk, Zm);
+                if (czz < Kz) {
+                    C2* o = A + f * AS + (size_t)x * K * KZP + czz;
+                    o[(size_t)kq * KZP] = Zk;                                  // mode kq
+                    if (kq > 0) o[(size_t)(kq + M - 1) * KZP] = Zm;            // mode kq - M
+                }
+            }
+        } else {
+            auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
+            auto store = [&](int q, C2 v) {
+                const int m = mode_of(q, N);
+                if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * KZP + cz] = v;
+            };
+            LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+        }
         __syncthreads();
     }
 }
@@ -982,7 +1058,8 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    load_tw(tw, twg, GE::tw_n);
+    using S3 = Split3<T, N>;
+    const C2* tw3 = load_tw_split<T, N>(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int L) {  // one thread
         const int t = blockIdx.x + (L / 3) * gridDim.x, f = L % 3, buf = L & 1;
@@ -1024,13 +1101,32 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             }
             C2* Sb = S + (size_t)buf * RS * CT;
             C2* Rf = Rt + f * K * CT;
-            auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
             auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
-            auto store = [&](int q, C2 v) {
-                const int m = mode_of(q, N);
-                if (m <= mmax && m >= -mmax) Rf[cidx_of(m, K) * CT + col] = v;
-            };
-            LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+            if constexpr (S3::on) {
+                // sub-line b = rows x = 3a + b, transformed in place; the kept
+                // modes by the radix-3 recombination
+                constexpr int M = S3::M;
+                const int sub = g / S3::GM, gm = g % S3::GM;
+                auto addr3 = [&](int p) { return (int)(Sb - S) + (3 * p + sub) * CT + col; };
+                auto store = [&](int p, C2 v) { S[addr3(p)] = v; };
+                LineFFT<T, M, -1>::template run<true>(S, tw, addr3, gm, noload, store);
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < M * CT; idx += blockDim.x) {
+                    const int kq = idx / CT, c = idx % CT;
+                    C2 Zk, Zm;
+                    split3_out(Sb[(3 * kq) * CT + c], Sb[(3 * kq + 1) * CT + c], Sb[(3 * kq + 2) * CT + c], tw3, kq,
+                               M, Zk, Zm);
+                    Rf[kq * CT + c] = Zk;                                 // mode kq
+                    if (kq > 0) Rf[(kq + M - 1) * CT + c] = Zm;           // mode kq - M
+                }
+            } else {
+                auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
+                auto store = [&](int q, C2 v) {
+                    const int m = mode_of(q, N);
+                    if (m <= mmax && m >= -mmax) Rf[cidx_of(m, K) * CT + col] = v;
+                };
+                LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
+            }
             __syncthreads();
         }
         if (stop) break;
