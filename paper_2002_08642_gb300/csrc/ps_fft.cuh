@@ -182,13 +182,21 @@ __host__ __device__ constexpr bool size_ok(int n) {
 }
 
 // ----------------------------------------------------------- line transform
+// Mask of this warp's lanes that exist (the block's last warp may be partial).
+__device__ __forceinline__ unsigned warp_lanes() {
+    const int left = (int)blockDim.x - (int)(threadIdx.x & ~31u);
+    return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
 // One length-N line per thread group of G = N / R0 threads. `addr(p)` maps
 // line position p to this thread's shared-memory slot of the tile; `load(p)`
 // feeds the first stage when FROM_TILE is false; `store(p, v)` receives the
 // last stage's outputs (natural order). The caller must __syncthreads()
 // before the call if the tile was in use; stage boundaries sync internally,
-// so every thread of the block must make the call.
-template <typename T, int N, int SIGN> struct LineFFT {
+// so every thread of the block must make the call. WS: every line's G
+// threads lie in one warp and touch only their own line's slots, so a warp
+// barrier separates the stages instead of a block barrier.
+template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     using C = cplx<T>;
     static constexpr int S = n_stages(N);
     static constexpr int R0 = radix_at(N, 0);
@@ -197,6 +205,12 @@ template <typename T, int N, int SIGN> struct LineFFT {
     static constexpr int RL = radix_at(N, S - 1);
     static constexpr int NBL = (N / RL + G - 1) / G;
     static constexpr int SLOTS = NBL * RL;
+    static_assert(!WS || (G <= 32 && 32 % G == 0), "warp-synchronous lines must not cross warps");
+
+    static __device__ __forceinline__ void sync() {
+        if constexpr (WS) __syncwarp(warp_lanes());
+        else __syncthreads();
+    }
 
     // BU: the last stage calls store(slot, position, value) with the
     // compile-time slot b * RL + u (butterfly b, output u), so a caller can
@@ -251,7 +265,7 @@ template <typename T, int N, int SIGN> struct LineFFT {
                 const int j = g + b * G;
                 if (on && (NB * G == NBF || j < NBF)) gather(j, v[b]);
             }
-            __syncthreads();
+            sync();
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int j = g + b * G;
@@ -281,7 +295,7 @@ template <typename T, int N, int SIGN> struct LineFFT {
                 }
             }
         }
-        if constexpr (!last) __syncthreads();
+        if constexpr (!last) sync();
         if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on);
     }
 

@@ -46,6 +46,10 @@
 #ifndef PS_Z3
 #define PS_Z3 1
 #endif
+// 1: z-pass line transforms whose threads fit in one warp sync by warp
+#ifndef PS_ZWS
+#define PS_ZWS 1
+#endif
 // tile width of the TMA-staged y passes (0 = automatic)
 #ifndef PS_TY_C
 #define PS_TY_C 0
@@ -376,6 +380,10 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     constexpr int M = Z3 ? N / 3 : N;
     constexpr int GM = LineFFT<T, M, 1>::G;        // threads per sub-line
     static_assert(!Z3 || G == 3 * GM, "three sub-lines per line group");
+    // a (sub-)line's threads are consecutive and start at a multiple of its
+    // thread count: if that count divides 32, its stages need warp barriers only
+    constexpr int GL = Z3 ? GM : G;
+    constexpr bool WS = PS_ZWS != 0 && GL <= 32 && 32 % GL == 0;
     constexpr int TWM = Z3 ? (tw_count(M) > 0 ? tw_count(M) : 1) : 0;
     const int b0 = kp.xs0 * N / LZ, b1 = (kp.xs0 + kp.xsn) * N / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
@@ -459,7 +467,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 return cmul(v, tw3[(sub - 1) * M + q]);
             };
             auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-            LineFFT<T, M, 1>::template run<false>(tiles, tw, addr, gm, load, store);
+            LineFFT<T, M, 1, WS>::template run<false>(tiles, tw, addr, gm, load, store);
         } else {
             const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
             const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
@@ -478,7 +486,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 return cmk<C2>((T)0, (T)0);
             };
             auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-            LineFFT<T, N, 1>::template run<false>(tiles, tw, addr, g, load, store);
+            LineFFT<T, N, 1, WS>::template run<false>(tiles, tw, addr, g, load, store);
         }
         __syncthreads();
         double fm[6] = {0, 0, 0, 0, 0, 0};
@@ -555,11 +563,11 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 const int sub = g / GM, gm = g % GM;
                 auto addr = [&](int p) { return tbase + zad(sub * M + p); };
                 auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
-                LineFFT<T, M, -1>::template run_masked<true>(tiles, tw, addr, gm, noload, store, active);
+                LineFFT<T, M, -1, WS>::template run_masked<true>(tiles, tw, addr, gm, noload, store, active);
             } else {
                 auto addr = [&](int p) { return tbase + zad(p); };
                 auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
-                LineFFT<T, N, -1>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
+                LineFFT<T, N, -1, WS>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
             }
         }
         __syncthreads();
