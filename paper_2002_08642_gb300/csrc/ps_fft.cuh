@@ -207,8 +207,9 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     static constexpr int SLOTS = NBL * RL;
     static_assert(!WS || (G <= 32 && 32 % G == 0), "warp-synchronous lines must not cross warps");
 
-    static __device__ __forceinline__ void sync() {
-        if constexpr (WS) __syncwarp(warp_lanes());
+    // stage barrier; lanes = the warp's lanes taking part (WS only)
+    static __device__ __forceinline__ void sync(unsigned lanes) {
+        if constexpr (WS) __syncwarp(lanes);
         else __syncthreads();
     }
 
@@ -217,7 +218,7 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     // keep a thread's outputs in registers; otherwise store(position, value).
     template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
-                                                 const Load& load, const Store& store, bool on = true) {
+                                                 const Load& load, const Store& store, bool on, unsigned lanes) {
         constexpr int r = radix_at(N, s);
         constexpr int Ls = ls_at(N, s);
         constexpr int NBF = N / r;
@@ -265,7 +266,7 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
                 const int j = g + b * G;
                 if (on && (NB * G == NBF || j < NBF)) gather(j, v[b]);
             }
-            sync();
+            sync(lanes);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int j = g + b * G;
@@ -295,26 +296,34 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
                 }
             }
         }
-        if constexpr (!last) sync();
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on);
+        if constexpr (!last) sync(lanes);
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on, lanes);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run(C* tile, const C* tw, const Addr& addr, int g,
                                                const Load& load, const Store& store) {
-        stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true);
+        stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
     }
     // Last-stage outputs delivered as store(slot, position, value).
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run_bu(C* tile, const C* tw, const Addr& addr, int g,
                                                   const Load& load, const Store& store) {
-        stage<0, FROM_TILE, true>(tile, tw, addr, g, load, store, true);
+        stage<0, FROM_TILE, true>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
     }
-    // Same, but threads with on == false only take part in the barriers.
+    // Same, for the threads with on == true. Block barriers: the others
+    // still take part in them. Warp barriers (WS): the others leave at once
+    // (on must be the same for all G threads of a line).
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run_masked(C* tile, const C* tw, const Addr& addr, int g,
                                                       const Load& load, const Store& store, bool on) {
-        stage<0, FROM_TILE>(tile, tw, addr, g, load, store, on);
+        if constexpr (WS) {
+            const unsigned lanes = __ballot_sync(warp_lanes(), on);
+            if (!on) return;
+            stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true, lanes);
+        } else {
+            stage<0, FROM_TILE>(tile, tw, addr, g, load, store, on, 0u);
+        }
     }
 };
 

@@ -40,7 +40,12 @@
 #define PS_ZP_SMEM_KB 100
 #endif
 #ifndef PS_ZP_MINB
-#define PS_ZP_MINB 0   // 0: 3 blocks per SM up to n = 256, 2 above
+#define PS_ZP_MINB 0   // 0: automatic (Geo::ZMINB)
+#endif
+// z-pass staging buffers: 2 = the next batch's copy overlaps the whole
+// batch; 1 = it is issued once the inverse transforms have read the buffer
+#ifndef PS_ZP_NBUF
+#define PS_ZP_NBUF 1
 #endif
 // 1: z lines of n = 3M done as three length-M transforms (see k_zpass)
 #ifndef PS_Z3
@@ -62,6 +67,10 @@
 #endif
 #ifndef PS_X1_SMEM_KB
 #define PS_X1_SMEM_KB 64
+#endif
+// x-forward update: points per thread whose U/H loads are issued together
+#ifndef PS_X5_UNR
+#define PS_X5_UNR 1
 #endif
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
@@ -146,10 +155,11 @@ template <typename T, int N> struct Geo {
     // kept z modes, padded to the tile width
     static constexpr int KZ = (N - 1) / 3 + 1;
     static constexpr int KZP = (KZ + CW - 1) / CW * CW;
-    // z pass: LZ lines per batch (even, divides n^2), 3 LZ G threads, two
-    // staging buffers of the batch's six spectral lines plus the FFT tiles
+    // z pass: LZ lines per batch (even, divides n^2), 3 LZ G threads,
+    // ZNB staging buffers of the batch's six spectral lines plus the FFT tiles
+    static constexpr int ZNB = PS_ZP_NBUF == 1 ? 1 : 2;
     static constexpr int zsmem(int l) {
-        return (int)sizeof(C2) * (2 * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1) + 128;
+        return (int)sizeof(C2) * (ZNB * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1) + 128;
     }
     static constexpr int lz_pick() {
         int l = 2;
@@ -158,7 +168,12 @@ template <typename T, int N> struct Geo {
         return l;
     }
     static constexpr int LZ = lz_pick();
-    static constexpr int ZMINB = PS_ZP_MINB > 0 ? PS_ZP_MINB : (N <= 256 ? 3 : 2);
+    // three blocks per SM where the register cap this sets (<= 72 at 288
+    // threads) costs no more than a few spilled words, else two; never more
+    // than the shared memory lets reside
+    static constexpr int ZFIT = (227 * 1024) / (zsmem(LZ) + 4096) > 0 ? (227 * 1024) / (zsmem(LZ) + 4096) : 1;
+    static constexpr int ZMIN0 = (3 * LZ * G <= 288 || N <= 256) ? 3 : 2;
+    static constexpr int ZMINB = PS_ZP_MINB > 0 ? PS_ZP_MINB : (ZMIN0 < ZFIT ? ZMIN0 : ZFIT);
     // TMA-staged y passes: K = kept x/y modes; inputs come in boxes of at
     // most 256 rows (NBOX boxes of BR rows cover R rows)
     static constexpr int K = 2 * ((N - 1) / 3) + 1;
@@ -388,12 +403,13 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     const int b0 = kp.xs0 * N / LZ, b1 = (kp.xs0 + kp.xsn) * N / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][6][LZ][KZP]
+    constexpr int NB = GE::ZNB;
+    C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [NB][6][LZ][KZP]
     if (smem_u32(stage) & 127u) {   // never expected: refuse to start copies
         if (threadIdx.x == 0) atomicExch(err, 2);
         return;
     }
-    C2* tiles = stage + 2 * 6 * LZ * KZP;                // [LZ][3][LP]
+    C2* tiles = stage + NB * 6 * LZ * KZP;               // [LZ][3][LP]
     C2* tw = tiles + 3 * LZ * LP;
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double wacc[32][12];     // per-warp (sum, compensation) of the six sums
@@ -431,15 +447,17 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     const T inv_eta = (T)kp.inv_eta;
     int it = 0;
     for (int b = b0 + blockIdx.x; b < b1; b += gridDim.x, ++it) {
-        const int buf = it & 1;
+        const int buf = NB == 2 ? (it & 1) : 0;
         const bool more = b + (int)gridDim.x < b1;
-        if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
-        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (NB == 2 && threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
+        const uint32_t par = NB == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
+        const bool ok = mbar_wait(&bar[buf], par);
         if (__syncthreads_or(!ok)) {
-            // a copy never completed: record it, let any other copy land, stop
+            // a copy never completed: record it, let any copy in flight land, stop
             if (threadIdx.x == 0) {
                 atomicExch(err, 1);
-                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+                if (NB == 1) mbar_wait(&bar[0], par);
+                else if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
             }
             break;
         }
@@ -489,6 +507,8 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             LineFFT<T, N, 1, WS>::template run<false>(tiles, tw, addr, g, load, store);
         }
         __syncthreads();
+        // one buffer: every read of it is done, the next batch may land
+        if (NB == 1 && threadIdx.x == 0 && more) issue(b + gridDim.x, 0);
         double fm[6] = {0, 0, 0, 0, 0, 0};
         bool touched = false;
         // n = u x w - (chi/eta)(u - us) of line l at z; forces in double
@@ -1140,10 +1160,8 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         if (stop) break;
         const T my = (T)cmode_of(cy, mmax, K);
         const T ey = Ex[cy];
-        for (int idx = threadIdx.x; idx < K * CT; idx += blockDim.x) {
-            const int cx = idx / CT, c = idx % CT;
-            const int czz = czt * CT + c;
-            if (czz >= Kz) continue;
+        // projected nonlinear term of point idx (the 1/n^3 applied)
+        auto proj = [&](int idx, int cx, int czz, C2* nn) {
             const int mx = cmode_of(cx, mmax, K);
             C2 n0 = Rt[idx], n1 = Rt[K * CT + idx], n2 = Rt[2 * K * CT + idx];
             n0.x *= invn3; n0.y *= invn3;
@@ -1162,27 +1180,55 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             } else if (MODE == 0 && !kp.mean_free) {
                 n0 = n1 = n2 = cmk<C2>((T)0, (T)0);
             }
-            const size_t o = ((size_t)cy * K + cx) * KZP + czz;
-            if constexpr (MODE == 1) {
-                U[o] = n0; U[FS + o] = n1; U[2 * FS + o] = n2;
-                const C2 z = cmk<C2>((T)0, (T)0);
-                H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
-            } else {
-                const T E = Ex[cx] * ey * Ez[czz];
-                const C2 nn[3] = {n0, n1, n2};
+            nn[0] = n0; nn[1] = n1; nn[2] = n2;
+        };
+        constexpr int UNR = MODE == 0 ? PS_X5_UNR : 1;
+        for (int i0 = threadIdx.x; i0 < K * CT; i0 += UNR * blockDim.x) {
+            // the U (and H) loads of UNR points first, then their updates
+            C2 uu[UNR][3], hh[UNR][3];
+            bool okp[UNR];
 #pragma unroll
-                for (int ff = 0; ff < 3; ++ff) {
-                    const C2 u = U[ff * FS + o];
-                    C2 r;
-                    if (first) {
-                        r = cmk<C2>(E * (u.x + dt * nn[ff].x), E * (u.y + dt * nn[ff].y));
-                    } else {
-                        const C2 h = H[ff * FS + o];
-                        const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
-                        r = cmk<C2>(E * u.x + a3 * nn[ff].x - a2 * h.x, E * u.y + a3 * nn[ff].y - a2 * h.y);
+            for (int r = 0; r < UNR; ++r) {
+                const int idx = i0 + r * blockDim.x;
+                const int cx = idx / CT, czz = czt * CT + idx % CT;
+                okp[r] = idx < K * CT && czz < Kz;
+                if (MODE == 0 && okp[r]) {
+                    const size_t o = ((size_t)cy * K + cx) * KZP + czz;
+#pragma unroll
+                    for (int ff = 0; ff < 3; ++ff) {
+                        uu[r][ff] = U[ff * FS + o];
+                        if (!first) hh[r][ff] = H[ff * FS + o];
                     }
-                    U[ff * FS + o] = r;
-                    H[ff * FS + o] = nn[ff];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < UNR; ++r) {
+                if (!okp[r]) continue;
+                const int idx = i0 + r * blockDim.x;
+                const int cx = idx / CT, czz = czt * CT + idx % CT;
+                C2 nn[3];
+                proj(idx, cx, czz, nn);
+                const size_t o = ((size_t)cy * K + cx) * KZP + czz;
+                if constexpr (MODE == 1) {
+                    U[o] = nn[0]; U[FS + o] = nn[1]; U[2 * FS + o] = nn[2];
+                    const C2 z = cmk<C2>((T)0, (T)0);
+                    H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
+                } else {
+                    const T E = Ex[cx] * ey * Ez[czz];
+#pragma unroll
+                    for (int ff = 0; ff < 3; ++ff) {
+                        const C2 u = uu[r][ff];
+                        C2 v;
+                        if (first) {
+                            v = cmk<C2>(E * (u.x + dt * nn[ff].x), E * (u.y + dt * nn[ff].y));
+                        } else {
+                            const C2 h = hh[r][ff];
+                            const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
+                            v = cmk<C2>(E * u.x + a3 * nn[ff].x - a2 * h.x, E * u.y + a3 * nn[ff].y - a2 * h.y);
+                        }
+                        U[ff * FS + o] = v;
+                        H[ff * FS + o] = nn[ff];
+                    }
                 }
             }
         }
