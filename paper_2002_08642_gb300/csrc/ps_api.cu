@@ -519,10 +519,10 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     }
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
-        if (!encode_rows(&c->tmA, c->b.A, c->fp64, (size_t)6 * n * Kk, kp.Kzp, ops->cy2, ops->br2) ||
+        if (!encode_planes(&c->tmA, c->b.A, c->fp64, kp.Kzp, (size_t)n, (size_t)6 * Kk, ops->cy2, ops->br2) ||
             !encode_rows(&c->tmB, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4, ops->br4) ||
             !encode_rows(&c->tmU, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2) ||
-            !encode_planes(&c->tmA5, c->b.A, c->fp64, kp.Kzp, (size_t)Kk, (size_t)6 * n, ops->cx5, ops->br4) ||
+            !encode_rows(&c->tmA5, c->b.A, c->fp64, (size_t)6 * Kk * n, kp.Kzp, ops->cx5, ops->br4) ||
             !encode_rows(&c->tmUp, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
             !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
             !encode_rows(&c->tmBo, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4o, ops->br4)) {

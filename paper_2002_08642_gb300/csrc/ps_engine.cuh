@@ -35,10 +35,10 @@ struct Bufs {
     void* Ez;        // exp(-nu kz^2 dt) for the Kz z modes (T)
     double* partial; // per-block partial sums
     int* err;        // device error flag (bounded waits that gave up)
-    const CUtensorMap* tmA;  // A as rows of 2 Kzp reals (y-inverse input)
+    const CUtensorMap* tmA;  // A as {2 Kzp reals, n rows, 6 K planes} (y-inverse input)
     const CUtensorMap* tmB;  // B as rows of 2 Kzp reals (y-forward input)
     const CUtensorMap* tmU;  // U as rows of 2 Kzp reals (x-inverse input)
-    const CUtensorMap* tmA5; // A as {2 Kzp, K, 6 n} (x-forward input)
+    const CUtensorMap* tmA5; // A as rows of 2 Kzp reals (x-forward input)
     const CUtensorMap* tmUp; // U, H as rows of 2 Kzp reals, x-forward box (L2 prefetch)
     const CUtensorMap* tmHp;
     const CUtensorMap* tmBo; // B, y-forward box of the slab pipeline

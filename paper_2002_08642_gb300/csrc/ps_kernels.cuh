@@ -9,8 +9,13 @@
 //          x/y index c in [0, K) <-> mode m = c (c <= mmax) or c - K,
 //          z index c in [0, Kz) <-> mode m = c; K = 2 mmax + 1, Kz = mmax + 1,
 //          mmax = (n - 1) / 3, Kzp = Kz rounded up to the tile width.
-//   A      after the x transform: nf x [n][K][Kzp]   (x physical, y/z spectral;
-//          also the y-forward output read by the x-forward pass)
+//   A      after the x transform: nf x [K][n][Kzp]   (y spectral, x physical,
+//          z spectral; also the y-forward output read by the x-forward pass).
+//          x lines of fixed ky are contiguous, so an x-pass tile stays within
+//          one n Kzp block; with x outermost instead, the x-inverse's stores
+//          of one tile spread over the whole field and it ran 1.6x slower at
+//          n = 768 (the y passes, whose tiles then stride by n Kzp per row,
+//          measured the same either way).
 //   B      after the y transform: nf x [n][n][Kzp]   (x/y physical, z spectral)
 //   chi    n^3 real, us 3 x n^3 real, line flag [n][n] (1 if the z line
 //          touches chi > 0)
@@ -179,6 +184,8 @@ template <typename T, int N> struct Geo {
     static constexpr int K = 2 * ((N - 1) / 3) + 1;
     static constexpr int nbox(int r) { return (r + 255) / 256; }
     static constexpr int brows(int r) { return (r + nbox(r) - 1) / nbox(r); }
+    // row of (x, ky) within a field of A: [ky][x], an x line is contiguous
+    static __host__ __device__ constexpr size_t arow(int x, int ky) { return (size_t)ky * N + x; }
     // smem rows between box starts: every box lands 128-byte aligned
     static constexpr int bpitch(int r, int c) {
         const int q = 128 / (c * (int)sizeof(C2)) > 0 ? 128 / (c * (int)sizeof(C2)) : 1;
@@ -323,7 +330,7 @@ k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx
             return cmk<C2>(-(kx * uy.y - ky * ux.y), kx * uy.x - ky * ux.x);
         };
         auto store = [&](int x, C2 v) {
-            if (okz) A[f * AS + ((size_t)x * K + cy) * Kzp + cz] = v;
+            if (okz) A[f * AS + GE::arow(x, cy) * Kzp + cz] = v;
         };
         LineFFT<T, N, 1>::template run<false>(tile, tw, addr, g, load, store);
     }
@@ -354,7 +361,7 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
         auto load = [&](int q) -> C2 {
             const int m = mode_of(q, N);
             if (!okz || m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
-            return A[f * AS + ((size_t)x * K + cidx_of(m, K)) * Kzp + cz];
+            return A[f * AS + GE::arow(x, cidx_of(m, K)) * Kzp + cz];
         };
         auto store = [&](int y, C2 v) {
             if (okz) B[f * BS + ((size_t)x * N + y) * Kzp + cz] = v;
@@ -664,7 +671,7 @@ k_yfwd(KP kp, const cplx<T>* __restrict__ B, cplx<T>* __restrict__ A, const cplx
         };
         auto store = [&](int q, C2 v) {
             const int m = mode_of(q, N);
-            if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * Kzp + cz] = v;
+            if (okz && m <= mmax && m >= -mmax) A[f * AS + GE::arow(x, cidx_of(m, K)) * Kzp + cz] = v;
         };
         LineFFT<T, N, -1>::template run<false>(tile, tw, addr, g, load, store);
     }
@@ -700,7 +707,7 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         __syncthreads();
         auto load = [&](int x) -> C2 {
             if (!okz) return cmk<C2>((T)0, (T)0);
-            return A[f * AS + ((size_t)x * K + cy) * Kzp + cz];
+            return A[f * AS + GE::arow(x, cy) * Kzp + cz];
         };
         auto store = [&](int q, C2 v) { tile[addr(q)] = v; };
         LineFFT<T, N, -1>::template run<false>(tile, tw, addr, g, load, store);
@@ -807,7 +814,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
-            tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * N + x) * K + b * BR, &bar[buf]);
+            tma_load_3d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, x, f * K + b * BR, &bar[buf]);
     };
     if (threadIdx.x == 0 && (int)blockIdx.x < NITEM) issue(blockIdx.x, 0);
     auto addr = [&](int p) { return p * CT + col; };
@@ -917,16 +924,16 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                 split3_out(Sb[(3 * kq) * CT + c], Sb[(3 * kq + 1) * CT + c], Sb[(3 * kq + 2) * CT + c], tw3, kq, M,
                            Zk, Zm);
                 if (czz < Kz) {
-                    C2* o = A + f * AS + (size_t)x * K * KZP + czz;
-                    o[(size_t)kq * KZP] = Zk;                                  // mode kq
-                    if (kq > 0) o[(size_t)(kq + M - 1) * KZP] = Zm;            // mode kq - M
+                    C2* o = A + f * AS + czz;
+                    o[GE::arow(x, kq) * KZP] = Zk;                             // mode kq
+                    if (kq > 0) o[GE::arow(x, kq + M - 1) * KZP] = Zm;         // mode kq - M
                 }
             }
         } else {
             auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
             auto store = [&](int q, C2 v) {
                 const int m = mode_of(q, N);
-                if (okz && m <= mmax && m >= -mmax) A[f * AS + ((size_t)x * K + cidx_of(m, K)) * KZP + cz] = v;
+                if (okz && m <= mmax && m >= -mmax) A[f * AS + GE::arow(x, cidx_of(m, K)) * KZP + cz] = v;
             };
             LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
         }
@@ -993,7 +1000,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         const bool okz = cz < Kz;
         const T ky = (T)(kp.ks * cmode_of(cy, mmax, K));
         const T kz = (T)(kp.ks * cz);
-        C2* out = A + ((size_t)cy) * KZP + cz;   // + f AS + x K KZP
+        C2* out = A + cz;   // + f AS + arow(x, cy) KZP
 #pragma unroll 1
         for (int f = 0; f < 3; ++f) {
             const int L = 3 * ti + f, buf = L & 1;
@@ -1021,7 +1028,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                     return cmk<C2>(-kx * v.y, kx * v.x);
                 };
                 auto store = [&](int slot, int x, C2 v) {
-                    C2* o = out + (size_t)x * K * KZP;
+                    C2* o = out + GE::arow(x, cy) * KZP;
                     if (f == 0) {                       // Ux
                         R1[slot] = v;
                         if (okz) o[0] = v;
@@ -1096,7 +1103,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
-            tma_load_3d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, cy, f * N + b * BR, &bar[buf]);
+            tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * K + cy) * N + b * BR, &bar[buf]);
     };
     if (threadIdx.x == 0) issue(0);
     const T s = (T)kp.ks;
