@@ -110,7 +110,7 @@ template <typename T, int N> struct Engine {
     static constexpr size_t sm_x5t = (size_t)GE::x5_smem(GE::CX5);
     static constexpr int thr_x1 = GE::CX1 * GE::G;
     static constexpr int thr_x5 = GE::CX5 * GE::G;
-    static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2);
+    static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2, GE::Y2NB);
     static constexpr size_t sm_y4 = (size_t)GE::y4_smem(GE::CY4);
     static constexpr int thr_y2 = GE::CY2 * GE::G;
     static constexpr int thr_y4 = GE::CY4 * GE::G;

@@ -216,9 +216,13 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     // BU: the last stage calls store(slot, position, value) with the
     // compile-time slot b * RL + u (butterfly b, output u), so a caller can
     // keep a thread's outputs in registers; otherwise store(position, value).
-    template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store>
+    struct NoHook {
+        __device__ __forceinline__ void operator()() const {}
+    };
+    template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store, class Hook = NoHook>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
-                                                 const Load& load, const Store& store, bool on, unsigned lanes) {
+                                                 const Load& load, const Store& store, bool on, unsigned lanes,
+                                                 const Hook& hook = Hook()) {
         constexpr int r = radix_at(N, s);
         constexpr int Ls = ls_at(N, s);
         constexpr int NBF = N / r;
@@ -297,13 +301,22 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
             }
         }
         if constexpr (!last) sync(lanes);
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on, lanes);
+        if constexpr (s == 0 && !last) hook();
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on, lanes, hook);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
     static __device__ __forceinline__ void run(C* tile, const C* tw, const Addr& addr, int g,
                                                const Load& load, const Store& store) {
         stage<0, FROM_TILE>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
+    }
+    // Same, and hook() is called by every thread right after the barrier
+    // that ends the first stage (every load() call done); a one-stage
+    // transform (S == 1) has no such barrier and never calls it.
+    template <bool FROM_TILE, class Addr, class Load, class Store, class Hook>
+    static __device__ __forceinline__ void run_hook(C* tile, const C* tw, const Addr& addr, int g,
+                                                    const Load& load, const Store& store, const Hook& hook) {
+        stage<0, FROM_TILE, false>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u, hook);
     }
     // Last-stage outputs delivered as store(slot, position, value).
     template <bool FROM_TILE, class Addr, class Load, class Store>

@@ -64,6 +64,11 @@
 #ifndef PS_TY_C
 #define PS_TY_C 0
 #endif
+// y-inverse staging buffers: 2 = the next item's copy overlaps the whole
+// item; 1 = it is issued once the first FFT stage has read the buffer
+#ifndef PS_Y2_NBUF
+#define PS_Y2_NBUF 1
+#endif
 #ifndef PS_Y2_SMEM_KB
 #define PS_Y2_SMEM_KB 226
 #endif
@@ -191,8 +196,9 @@ template <typename T, int N> struct Geo {
         const int q = 128 / (c * (int)sizeof(C2)) > 0 ? 128 / (c * (int)sizeof(C2)) : 1;
         return (brows(r) + q - 1) / q * q;
     }
-    static constexpr int y2_smem(int c) {   // y inverse: 2 staging (K rows) + work tile (N rows)
-        return (int)sizeof(C2) * c * (2 * nbox(K) * bpitch(K, c) + N) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
+    static constexpr int Y2NB = PS_Y2_NBUF == 1 ? 1 : 2;
+    static constexpr int y2_smem(int c, int nb = 2) {   // y inverse: nb staging (K rows) + work tile (N rows)
+        return (int)sizeof(C2) * c * (nb * nbox(K) * bpitch(K, c) + N) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
     static constexpr int y4_smem(int c) {   // y forward: 2 staging tiles of N rows, transformed in place
         return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c)) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
@@ -204,7 +210,9 @@ template <typename T, int N> struct Geo {
     static constexpr int pick_c(int which, int kb, int cmax) {
         if (PS_TY_C > 0) return PS_TY_C;
         int c = cmax < CW ? cmax : CW;
-        while (c > 2 && (which == 2 ? y2_smem(c) : which == 4 ? y4_smem(c) : x5_smem(c)) > kb * 1024) c /= 2;
+        while (c > 2 && (which == 1 ? y2_smem(c) : which == 2 ? y2_smem(c, Y2NB) : which == 4 ? y4_smem(c) : x5_smem(c)) >
+                            kb * 1024)
+            c /= 2;
         return c;
     }
     // budgets measured on GB300 (FP32 and FP64 alike): the y passes and the
@@ -212,7 +220,7 @@ template <typename T, int N> struct Geo {
     // sets of outputs per thread) several narrow ones
     static constexpr int CY2 = pick_c(2, PS_Y2_SMEM_KB, 16);
     static constexpr int CY4 = pick_c(4, PS_Y4_SMEM_KB, 16);
-    static constexpr int CX1 = pick_c(2, PS_X1_SMEM_KB, 16);
+    static constexpr int CX1 = pick_c(1, PS_X1_SMEM_KB, 16);   // same smem shape as the y inverse, two buffers
     static constexpr int CX5 = pick_c(5, PS_X5_SMEM_KB, 128 / 16);
     // y-forward tile when it shares SMs with the z pass (slab pipeline)
     static constexpr int CY4O = pick_c(4, PS_Y4O_SMEM_KB, 16);
@@ -791,12 +799,13 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     const int NITEM = kp.xsn * NTZ * 6;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
+    constexpr int NB = GE::Y2NB;
+    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [NB][RS][CT]
     if (smem_u32(S) & 127u) {   // never expected: refuse to start copies
         if (threadIdx.x == 0) atomicExch(err, 2);
         return;
     }
-    C2* W = S + 2 * RS * CT;                              // [N][CT]
+    C2* W = S + NB * RS * CT;                             // [N][CT]
     C2* tw = W + N * CT;
     __shared__ __align__(8) uint64_t bar[2];
     const int col = threadIdx.x % CT, g = threadIdx.x / CT;
@@ -819,15 +828,18 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     if (threadIdx.x == 0 && (int)blockIdx.x < NITEM) issue(blockIdx.x, 0);
     auto addr = [&](int p) { return p * CT + col; };
     int it = 0;
+    using FFT = LineFFT<T, N, 1>;
     for (int i = blockIdx.x; i < NITEM; i += gridDim.x, ++it) {
-        const int buf = it & 1;
+        const int buf = NB == 2 ? (it & 1) : 0;
         const bool more = i + (int)gridDim.x < NITEM;
-        if (threadIdx.x == 0 && more) issue(i + gridDim.x, buf ^ 1);
-        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (NB == 2 && threadIdx.x == 0 && more) issue(i + gridDim.x, buf ^ 1);
+        const uint32_t par = NB == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
+        const bool ok = mbar_wait(&bar[buf], par);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicExch(err, 1);
-                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+                if (NB == 1) mbar_wait(&bar[0], par);
+                else if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
             }
             break;
         }
@@ -844,8 +856,18 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         auto store = [&](int y, C2 v) {
             if (okz) B[f * BS + ((size_t)x * N + y) * KZP + cz] = v;
         };
-        LineFFT<T, N, 1>::template run<false>(W, tw, addr, g, load, store);
-        __syncthreads();
+        if constexpr (NB == 1 && FFT::S > 1) {
+            // one buffer: refill it once the first stage has read it
+            auto refill = [&]() {
+                if (threadIdx.x == 0 && more) issue(i + gridDim.x, 0);
+            };
+            FFT::template run_hook<false>(W, tw, addr, g, load, store, refill);
+            __syncthreads();
+        } else {
+            FFT::template run<false>(W, tw, addr, g, load, store);
+            __syncthreads();
+            if (NB == 1 && threadIdx.x == 0 && more) issue(i + gridDim.x, 0);
+        }
     }
 }
 
