@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     # revolving flexible elliptic wing, FP32 bulk, mask rasterised every step
     "wing768": dict(n=768, L=4.0, nodes=2000, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
+    "wing384": dict(n=384, L=4.0, nodes=2000, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
     "wing256": dict(n=256, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
     "wing128": dict(n=128, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
 }
