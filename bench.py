@@ -52,7 +52,7 @@ def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4):
         "y_inverse": (6 * nk + 6 * nn) * e,
         "z_c2r_nonlinear_r2c": (6 * nn + 3 * nn) * e + mask,
         "y_forward": (3 * nn + 3 * nk) * e,
-        "x_forward_project_ab2": (3 * nk + 3 * kk + 3 * kk + 6 * kk) * e,
+        "x_forward_project_ab2": (3 * nk + 3 * kk + 6 * kk) * e,   # reads N, Q; writes U, Q
     }
 
 

@@ -3,7 +3,8 @@
 // (Sec. 4.1, Eq. penalized Navier--Stokes; time stepping paragraph).
 //
 // Storage (element = complex T unless stated):
-//   U, H   spectral velocity c_k = DFT(u)_k / n^3 and AB2 history N^{n-1},
+//   U, H   spectral velocity c_k = DFT(u)_k / n^3 and AB2 history
+//          Q^n = E U^n - (dt/2) E^2 N^{n-1} (see ab2_update),
 //          3 x [K (ky)][K (kx)][Kzp] (an x line of fixed ky, kz is a
 //          contiguous block), only the modes the 2/3 rule keeps:
 //          x/y index c in [0, K) <-> mode m = c (c <= mmax) or c - K,
@@ -272,6 +273,24 @@ __device__ __forceinline__ void split3_out(C2 F0, C2 F1, C2 F2, const C2* tw3, i
     // e^{-2 pi i 2/3} = (-1/2, +h), e^{-2 pi i 4/3} = (-1/2, -h)
     Zm = cmk<C2>(F0.x - (T)0.5 * (G1.x + G2.x) - h3 * (G1.y - G2.y),
                  F0.y - (T)0.5 * (G1.y + G2.y) + h3 * (G1.x - G2.x));
+}
+
+// Integrating-factor AB2 update of one mode (Sec. 4.1, time stepping):
+// U^{n+1} = E U^n + (dt/2)(3 E N^n - E^2 N^{n-1}). The history array holds
+// Q^n = E U^n - (dt/2) E^2 N^{n-1}, the part of U^{n+1} known before N^n, so
+// a step reads one array: U^{n+1} = Q^n + (3/2) dt E N^n (Euler start:
+// U^1 = E (U^0 + dt N^0), reading U^0), then Q^{n+1} = E U^{n+1} - (dt/2) E^2 N^n.
+// uq = Q^n (U^0 on the first step), nn = N^n.
+template <typename C2, typename T>
+__device__ __forceinline__ void ab2_update(C2 uq, C2 nn, T E, T dt, bool first, C2& unew, C2& qnew) {
+    if (first) {
+        unew = cmk<C2>(E * (uq.x + dt * nn.x), E * (uq.y + dt * nn.y));
+    } else {
+        const T a3 = (T)1.5 * dt * E;
+        unew = cmk<C2>(uq.x + a3 * nn.x, uq.y + a3 * nn.y);
+    }
+    const T a2 = (T)0.5 * dt * E * E;
+    qnew = cmk<C2>(E * unew.x - a2 * nn.x, E * unew.y - a2 * nn.y);
 }
 
 // Twiddles into shared memory: the n-line table, or for the n = 3M split
@@ -764,17 +783,11 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
             C2 nn[3] = {n0, n1, n2};
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const C2 u = U[f * FS + o];
-                C2 r;
-                if (first) {
-                    r = cmk<C2>(E * (u.x + dt * nn[f].x), E * (u.y + dt * nn[f].y));
-                } else {
-                    const C2 h = H[f * FS + o];
-                    const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
-                    r = cmk<C2>(E * u.x + a3 * nn[f].x - a2 * h.x, E * u.y + a3 * nn[f].y - a2 * h.y);
-                }
-                U[f * FS + o] = r;
-                H[f * FS + o] = nn[f];
+                const C2 uq = first ? U[f * FS + o] : H[f * FS + o];
+                C2 un, qn;
+                ab2_update(uq, nn[f], E, dt, first != 0, un, qn);
+                U[f * FS + o] = un;
+                H[f * FS + o] = qn;
             }
         }
     }
@@ -1140,8 +1153,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         // start pulling them into L2 now
         if (MODE == 0 && threadIdx.x < 3 * NBK) {
             const int f = threadIdx.x / NBK, b = threadIdx.x % NBK;
-            tma_prefetch_2d(&tmu, 2 * czt * CT, (f * K + cy) * K + b * BRK);
-            if (!first) tma_prefetch_2d(&tmh, 2 * czt * CT, (f * K + cy) * K + b * BRK);
+            tma_prefetch_2d(first ? &tmu : &tmh, 2 * czt * CT, (f * K + cy) * K + b * BRK);
         }
 #pragma unroll 1
         for (int f = 0; f < 3; ++f) {
@@ -1214,7 +1226,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         constexpr int UNR = MODE == 0 ? PS_X5_UNR : 1;
         for (int i0 = threadIdx.x; i0 < K * CT; i0 += UNR * blockDim.x) {
             // the U (and H) loads of UNR points first, then their updates
-            C2 uu[UNR][3], hh[UNR][3];
+            C2 uq[UNR][3];
             bool okp[UNR];
 #pragma unroll
             for (int r = 0; r < UNR; ++r) {
@@ -1224,10 +1236,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
                 if (MODE == 0 && okp[r]) {
                     const size_t o = ((size_t)cy * K + cx) * KZP + czz;
 #pragma unroll
-                    for (int ff = 0; ff < 3; ++ff) {
-                        uu[r][ff] = U[ff * FS + o];
-                        if (!first) hh[r][ff] = H[ff * FS + o];
-                    }
+                    for (int ff = 0; ff < 3; ++ff) uq[r][ff] = first ? U[ff * FS + o] : H[ff * FS + o];
                 }
             }
 #pragma unroll
@@ -1246,17 +1255,10 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
                     const T E = Ex[cx] * ey * Ez[czz];
 #pragma unroll
                     for (int ff = 0; ff < 3; ++ff) {
-                        const C2 u = uu[r][ff];
-                        C2 v;
-                        if (first) {
-                            v = cmk<C2>(E * (u.x + dt * nn[ff].x), E * (u.y + dt * nn[ff].y));
-                        } else {
-                            const C2 h = hh[r][ff];
-                            const T a3 = (T)1.5 * dt * E, a2 = (T)0.5 * dt * E * E;
-                            v = cmk<C2>(E * u.x + a3 * nn[ff].x - a2 * h.x, E * u.y + a3 * nn[ff].y - a2 * h.y);
-                        }
-                        U[ff * FS + o] = v;
-                        H[ff * FS + o] = nn[ff];
+                        C2 un, qn;
+                        ab2_update(uq[r][ff], nn[ff], E, dt, first != 0, un, qn);
+                        U[ff * FS + o] = un;
+                        H[ff * FS + o] = qn;
                     }
                 }
             }
