@@ -304,7 +304,8 @@ def run_ours(args, cfg):
     peak, src = peaks()
     achieved = ab[top] / (tms / tl / 1e3) / 1e9
     step_bytes = sum(ab.values())
-    kernels_per_step = 5 + 6
+    # five passes + rasteriser (clear, nodes, tris, prefix, scatter1, scatter2, eval)
+    kernels_per_step = 5 + 7
     out = {
         "metric": "Mpts*steps/s", "value": value, "unit": "Mpts*steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

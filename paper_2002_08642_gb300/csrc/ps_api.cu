@@ -377,7 +377,8 @@ cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag,
         *par_out = np;  // both lists empty: the next call must clear densely
         return cudaGetLastError();
     }
-    k_mask_boxes<<<1, 1024, 0, s>>>(m, a, a.tw + a.h);
+    k_mask_tris<T><<<a.n_tri > 0 ? (a.n_tri + 127) / 128 : 1, 128, 0, s>>>(m, a, a.tw + a.h);
+    k_mask_prefix<<<1, 1024, 0, s>>>(m, a);
     k_mask_scatter1<T><<<2432, 256, 0, s>>>(m, a, np);
     k_mask_scatter2<T><<<2432, 256, 0, s>>>(m, a);
     k_mask_eval<T><<<1216, 256, 0, s>>>(m, a, np, (T*)chi, (T*)us, flag);

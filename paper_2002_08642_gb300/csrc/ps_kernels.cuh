@@ -330,8 +330,9 @@ k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx
     const bool okz = cz < kp.Kz;
     const int cy = blockIdx.y;
     const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
-    const T ky = (T)(kp.ks * cmode_of(cy, mmax, K));
-    const T kz = (T)(kp.ks * cz);
+    const T ks = (T)kp.ks;   // wavenumbers in T: no double arithmetic per element
+    const T ky = ks * (T)cmode_of(cy, mmax, K);
+    const T kz = ks * (T)cz;
     const size_t FS = (size_t)K * K * Kzp;
     const size_t AS = (size_t)N * K * Kzp;
     load_tw(tw, twg, GE::tw_n);
@@ -343,7 +344,7 @@ k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx
             const int m = mode_of(q, N);
             if (!okz || m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
             const size_t o = ((size_t)cy * K + cidx_of(m, K)) * Kzp + cz;
-            const T kx = (T)(kp.ks * m);
+            const T kx = ks * (T)m;
             if (f < 3) return U[f * FS + o];
             if (f == 3) {  // i (ky uz - kz uy)
                 C2 uy = U[FS + o], uz = U[2 * FS + o];
@@ -1006,6 +1007,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     __shared__ __align__(8) uint64_t bar[2];
     const int col = threadIdx.x % CT, g = threadIdx.x / CT;
     const int mmax = kp.mmax, Kz = kp.Kz;
+    const T ks = (T)kp.ks;   // wavenumbers in T: no double arithmetic per element
     const size_t AS = (size_t)N * K * KZP;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -1033,8 +1035,8 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         const int cy = t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
-        const T ky = (T)(kp.ks * cmode_of(cy, mmax, K));
-        const T kz = (T)(kp.ks * cz);
+        const T ky = ks * (T)cmode_of(cy, mmax, K);
+        const T kz = ks * (T)cz;
         C2* out = A + cz;   // + f AS + arow(x, cy) KZP
 #pragma unroll 1
         for (int f = 0; f < 3; ++f) {
@@ -1059,7 +1061,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                     const int c = cidx_of(m, K);
                     const C2 v = Sb[((c / BR) * BP + c % BR) * CT + col];
                     if (d == 0) return v;
-                    const T kx = (T)(kp.ks * m);
+                    const T kx = ks * (T)m;
                     return cmk<C2>(-kx * v.y, kx * v.x);
                 };
                 auto store = [&](int slot, int x, C2 v) {

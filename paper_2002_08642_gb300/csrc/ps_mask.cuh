@@ -13,8 +13,10 @@
 //   clear     zero chi/u_s and reset the per-point keys of the points the
 //             previous call touched (list kept in the workspace);
 //   nodes     global node positions X_O + R x^(w) (double);
-//   boxes     per-triangle grid-index bounding boxes and an exclusive prefix
-//             sum of their point counts (one block);
+//   tris      per triangle (one thread each): grid-index bounding box and
+//             the geometry the pair tests need, in the context precision:
+//             vertex a as grid cell + offset, edges b - a and c - a;
+//   prefix    exclusive prefix sum of the box point counts (one block);
 //   scatter1  for every (triangle, box point) pair with distance < reach:
 //             atomicMin of the distance bits (non-negative IEEE values order
 //             like their bit patterns); the first writer appends the point
@@ -47,13 +49,23 @@ struct MaskArgs {
 static constexpr int kMaskMaxTri = 1 << 17;
 static constexpr int kMaskMaxNodes = 1 << 17;
 
+// Per-triangle geometry of the pair tests: vertex a = ca dx + f per axis (ca
+// its grid cell index, f in [0, dx) the rest), edges b - a and c - a; the
+// lengths rounded once from double to T. A grid point minus a is then
+// (i - ca) dx - f, with no double arithmetic per pair.
+template <typename T> struct TriGeo {
+    int ca[4];
+    T f[3], b[3], c[3];
+};
+static constexpr size_t kTriGeoBytes = 128;   // >= sizeof(TriGeo<double>)
+
 // Workspace: keys (8 B/pt), winner ids (4 B/pt), two touched lists (4 B/pt
 // each), counters, node and triangle scratch.
 inline size_t mask_workspace_bytes(int n) {
     const size_t n3 = (size_t)n * n * n;
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
     return a(n3 * 8) + a(n3 * 4) + 2 * a(n3 * 4) + a(64) + a((size_t)kMaskMaxNodes * 3 * 8) +
-           a((size_t)kMaskMaxTri * 8 * 4) + a(((size_t)kMaskMaxTri + 1) * 8);
+           a((size_t)kMaskMaxTri * 8 * 4) + a(((size_t)kMaskMaxTri + 1) * 8) + a((size_t)kMaskMaxTri * kTriGeoBytes);
 }
 
 struct MaskWs {
@@ -62,8 +74,9 @@ struct MaskWs {
     uint32_t* list[2];
     unsigned long long* cnt;  // [0],[1]: list lengths, [2]: total pairs, [4]: bad-index flag
     double* xg;
-    int32_t* box;              // per triangle: i0,j0,k0,ei,ej,ek (+2 pad)
+    int32_t* box;              // per triangle: i0,j0,k0,ei,ej,ek, point count (+1 pad)
     unsigned long long* pre;   // exclusive prefix of box sizes (n_tri + 1)
+    unsigned char* geo;        // per triangle: TriGeo<T> in kTriGeoBytes
 };
 
 inline MaskWs mask_ws_split(unsigned char* w, int n) {
@@ -78,7 +91,8 @@ inline MaskWs mask_ws_split(unsigned char* w, int n) {
     m.cnt = (unsigned long long*)(w + o); o += a(64);
     m.xg = (double*)(w + o); o += a((size_t)kMaskMaxNodes * 3 * 8);
     m.box = (int32_t*)(w + o); o += a((size_t)kMaskMaxTri * 8 * 4);
-    m.pre = (unsigned long long*)(w + o);
+    m.pre = (unsigned long long*)(w + o); o += a(((size_t)kMaskMaxTri + 1) * 8);
+    m.geo = w + o;
     return m;
 }
 
@@ -166,58 +180,88 @@ __global__ void k_mask_nodes(MaskWs m, MaskArgs a) {
     }
 }
 
-// One block: boxes and their exclusive prefix sum (sequential chunks per
-// thread, then a serial pass over the chunk totals).
-__global__ void k_mask_boxes(MaskWs m, MaskArgs a, double reach) {
-    __shared__ unsigned long long part[1024];
+// One thread per triangle: bounding box dilated by the reach, its point
+// count, and the pair-test geometry.
+template <typename T>
+__global__ void k_mask_tris(MaskWs m, MaskArgs a, double reach) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tri) return;
+    int ok = 1;
+    int id[3];
+    double lo[3], hi[3];
+    for (int r = 0; r < 3; ++r) { lo[r] = 1e300; hi[r] = -1e300; }
+    for (int v = 0; v < 3; ++v) {
+        id[v] = a.tri[3 * t + v];
+        if (id[v] < 0 || id[v] >= a.n_nodes) { ok = 0; break; }
+        for (int r = 0; r < 3; ++r) {
+            const double q = m.xg[3 * id[v] + r];
+            lo[r] = fmin(lo[r], q);
+            hi[r] = fmax(hi[r], q);
+        }
+    }
+    int e[3] = {0, 0, 0}, i0[3] = {0, 0, 0};
+    TriGeo<T> gt;
+    for (int r = 0; r < 3; ++r) { gt.ca[r] = 0; gt.f[r] = gt.b[r] = gt.c[r] = (T)0; }
+    gt.ca[3] = 0;
+    if (ok) {
+        for (int r = 0; r < 3; ++r) {
+            double l = ceil((lo[r] - reach) / a.dx), h = floor((hi[r] + reach) / a.dx);
+            l = fmax(l, 0.0);
+            h = fmin(h, (double)(a.n - 1));
+            i0[r] = (int)l;
+            e[r] = h >= l ? (int)(h - l) + 1 : 0;
+            const double ar = m.xg[3 * id[0] + r];
+            const double cr = floor(ar / a.dx);
+            gt.ca[r] = (int)cr;
+            gt.f[r] = (T)(ar - cr * a.dx);
+            gt.b[r] = (T)(m.xg[3 * id[1] + r] - ar);
+            gt.c[r] = (T)(m.xg[3 * id[2] + r] - ar);
+        }
+    } else {
+        m.cnt[4] = 1;
+    }
+    int* b = m.box + 8 * t;
+    b[0] = i0[0]; b[1] = i0[1]; b[2] = i0[2];
+    b[3] = e[0]; b[4] = e[1]; b[5] = e[2];
+    b[6] = e[0] * e[1] * e[2];
+    *reinterpret_cast<TriGeo<T>*>(m.geo + (size_t)t * kTriGeoBytes) = gt;
+}
+
+// One block of 1024 threads: exclusive prefix sum of the box point counts
+// (per-thread chunks, then a scan of the chunk totals by warp shuffles).
+__global__ void k_mask_prefix(MaskWs m, MaskArgs a) {
+    __shared__ unsigned long long wsum[32];
     const int nt = a.n_tri;
     const int per = (nt + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per, t1 = min(nt, t0 + per);
     unsigned long long local = 0;
-    for (int t = t0; t < t1; ++t) {
-        int ok = 1;
-        double lo[3], hi[3];
-        for (int r = 0; r < 3; ++r) { lo[r] = 1e300; hi[r] = -1e300; }
-        for (int v = 0; v < 3; ++v) {
-            const int id = a.tri[3 * t + v];
-            if (id < 0 || id >= a.n_nodes) { ok = 0; break; }
-            for (int r = 0; r < 3; ++r) {
-                const double q = m.xg[3 * id + r];
-                lo[r] = fmin(lo[r], q);
-                hi[r] = fmax(hi[r], q);
-            }
-        }
-        int e[3] = {0, 0, 0}, i0[3] = {0, 0, 0};
-        if (ok) {
-            for (int r = 0; r < 3; ++r) {
-                double l = ceil((lo[r] - reach) / a.dx), h = floor((hi[r] + reach) / a.dx);
-                l = fmax(l, 0.0);
-                h = fmin(h, (double)(a.n - 1));
-                i0[r] = (int)l;
-                e[r] = h >= l ? (int)(h - l) + 1 : 0;
-            }
-        } else {
-            m.cnt[4] = 1;
-        }
-        int* b = m.box + 8 * t;
-        b[0] = i0[0]; b[1] = i0[1]; b[2] = i0[2];
-        b[3] = e[0]; b[4] = e[1]; b[5] = e[2];
-        local += (unsigned long long)e[0] * e[1] * e[2];
+    for (int t = t0; t < t1; ++t) local += (unsigned long long)m.box[8 * t + 6];
+    // inclusive scan within the warp, then of the warp totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long inc = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
     }
-    part[threadIdx.x] = local;
+    if (lane == 31) wsum[wid] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i) { const unsigned long long v = part[i]; part[i] = run; run += v; }
-        m.cnt[2] = run;
-        m.pre[nt] = run;
+    if (wid == 0) {
+        unsigned long long w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;   // inclusive totals of warps 0..lane
     }
     __syncthreads();
-    unsigned long long run = part[threadIdx.x];
+    unsigned long long run = inc - local + (wid > 0 ? wsum[wid - 1] : 0ull);
+    if (threadIdx.x == blockDim.x - 1) {
+        m.cnt[2] = run + local;
+        m.pre[nt] = run + local;
+    }
     for (int t = t0; t < t1; ++t) {
         m.pre[t] = run;
-        const int* b = m.box + 8 * t;
-        run += (unsigned long long)b[3] * b[4] * b[5];
+        run += (unsigned long long)m.box[8 * t + 6];
     }
 }
 
@@ -234,18 +278,18 @@ template <typename T>
 __device__ __forceinline__ bool pair_dist(const MaskWs& m, const MaskArgs& a, int t, unsigned long long local,
                                           uint32_t* pt, T* dist) {
     const int* b = m.box + 8 * t;
-    const unsigned long long ek = b[5], ej = b[4];
-    const int k = b[2] + (int)(local % ek);
-    const int j = b[1] + (int)((local / ek) % ej);
-    const int i = b[0] + (int)(local / (ek * ej));
-    const double px = i * a.dx, py = j * a.dx, pz = k * a.dx;
-    const int ia = a.tri[3 * t], ib = a.tri[3 * t + 1], ic = a.tri[3 * t + 2];
-    // relative to vertex a in double, then the context precision
-    const double ax = m.xg[3 * ia], ay = m.xg[3 * ia + 1], az = m.xg[3 * ia + 2];
-    T P[3] = {(T)(px - ax), (T)(py - ay), (T)(pz - az)};
+    const uint32_t l = (uint32_t)local, ek = (uint32_t)b[5], ej = (uint32_t)b[4];
+    const uint32_t q = l / ek;
+    const int k = b[2] + (int)(l - q * ek);
+    const int j = b[1] + (int)(q % ej);
+    const int i = b[0] + (int)(q / ej);
+    const TriGeo<T>& g = *reinterpret_cast<const TriGeo<T>*>(m.geo + (size_t)t * kTriGeoBytes);
+    // grid point minus vertex a, from whole cells and the vertex offset
+    const T dx = (T)a.dx;
+    T P[3] = {(T)(i - g.ca[0]) * dx - g.f[0], (T)(j - g.ca[1]) * dx - g.f[1], (T)(k - g.ca[2]) * dx - g.f[2]};
     T A0[3] = {(T)0, (T)0, (T)0};
-    T B0[3] = {(T)(m.xg[3 * ib] - ax), (T)(m.xg[3 * ib + 1] - ay), (T)(m.xg[3 * ib + 2] - az)};
-    T C0[3] = {(T)(m.xg[3 * ic] - ax), (T)(m.xg[3 * ic + 1] - ay), (T)(m.xg[3 * ic + 2] - az)};
+    T B0[3] = {g.b[0], g.b[1], g.b[2]};
+    T C0[3] = {g.c[0], g.c[1], g.c[2]};
     T bary[3];
     const T d = sqrt(closest_tri<T>(P, A0, B0, C0, bary));
     *pt = (uint32_t)(((size_t)i * a.n + j) * a.n + k);

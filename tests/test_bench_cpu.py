@@ -13,8 +13,13 @@ import bench
 def test_algorithmic_bytes_model():
     ab = bench.algorithmic_bytes(768, 8)
     total = sum(ab.values())
-    # ~98 bytes per grid point per step with the 2/3-truncated storage
-    assert 95 < total / 768 ** 3 < 100
+    # kept modes only: K = 511 x/y modes, Kz = 256 z modes; per step the five
+    # passes move 12 K^2 Kz + 18 n K Kz + 18 n^2 Kz complex values (the AB2
+    # update reads one history array) plus the n^2 line flags
+    K, Kz, n = 511, 256, 768
+    assert total == (12 * K * K * Kz + 18 * n * K * Kz + 18 * n * n * Kz) * 8 + n * n
+    # ~94 bytes per grid point per step
+    assert 93 < total / 768 ** 3 < 96
     assert max(ab, key=ab.get) == "y_inverse"
 
 
