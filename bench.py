@@ -348,6 +348,36 @@ def run_ours(args, cfg):
                             "fp32_speedup": value / v64}
         del g64
         torch.cuda.empty_cache()
+    if args.small and world == 1 and n != 256:
+        # the 256^3 revolving-wing configuration (600 nodes), FP32 and FP64 steps
+        c2 = WORKLOADS["wing256"]
+        tri2, seq2 = wing_inputs(c2, 24)
+        tri2_d = torch.from_numpy(tri2).to(dev, torch.int32)
+        res = {}
+        for prec, dt_, ks in (("fp32", torch.float32, 20), ("fp64", torch.float64, 8)):
+            g2 = Solver(c2["n"], c2["L"], c2["nu"], c2["eta"], c2["dt"], precision=prec, device=dev)
+            g2.set_velocity(torch.zeros((3, c2["n"], c2["n"], c2["n"]), dtype=dt_, device=dev))
+            xs = [torch.from_numpy(q[0]).to(dev, torch.float64) for q in seq2]
+            vs = [torch.from_numpy(q[1]).to(dev, torch.float64) for q in seq2]
+            for k in range(3):
+                g2.set_mask_from_nodes(xs[k], vs[k], tri2_d, seq2[k][2])
+                g2.step(1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for k in range(3, 3 + ks):
+                g2.set_mask_from_nodes(xs[k], vs[k], tri2_d, seq2[k][2])
+                g2.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            m2 = e0.elapsed_time(e1) / ks
+            res[prec] = (c2["n"] ** 3 / (m2 / 1e3) / 1e6, m2, ks)
+            del g2
+            torch.cuda.empty_cache()
+        out["wing256_step"] = {"value": res["fp32"][0], "unit": "Mpts*steps/s", "ms_per_step": res["fp32"][1],
+                               "steps": res["fp32"][2], "fp64_value": res["fp64"][0],
+                               "fp64_ms_per_step": res["fp64"][1], "fp64_steps": res["fp64"][2],
+                               "fp32_speedup": res["fp32"][0] / res["fp64"][0],
+                               "note": "256^3 revolving wing, 600 nodes, rasterise + step, inputs resident"}
     if args.adjoint and world == 1:
         # adjoint step throughput at 512^3 (FP32): one reversed step per call,
         # on the state and mask reached by a few forward steps
@@ -398,6 +428,7 @@ def main():
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    ap.add_argument("--no-256", dest="small", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

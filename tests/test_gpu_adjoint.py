@@ -163,3 +163,95 @@ def test_time_averaged_lift_gradient_vs_central_differences():
     errs = np.array(errs)
     print("node gradient vs FD: median rel err %.2e, max %.2e" % (np.median(errs), errs.max()))
     assert np.median(errs) < 1e-4 and np.mean(errs < 1e-2) > 0.8
+
+
+def _wing_window(n, L, K, nodes, u0, dtype, dt):
+    xw0, tri = inputs.elliptic_wing_mesh(nodes)
+    amp = inputs.flapping_amplitudes(xw0)
+    seq = [inputs.revolving_wing(k * dt, xw0, amp) for k in range(K)]
+    win = WingWindow(dev(tri, torch.int32), [dev(s[0] - xw0, torch.float64) for s in seq],
+                     [dev(s[1], torch.float64) for s in seq], [s[2] for s in seq], dev(u0, dtype))
+    return xw0, tri, seq, win
+
+
+def test_lift_gradient_matches_oracle_gradient():
+    """32^3 revolving wing, 8-step window (checkpoint every 4), FP64: the
+    library's d(mean lift)/d(node positions) against the oracle's: oracle
+    forward over the rasterised masks, oracle adjoint, oracle rasteriser
+    transpose, summed over the window."""
+    n, L, nu, eta, dt = 32, 4.0, 1.527e-4, 1e-2, 5e-4
+    K, every, dx = 8, 4, 4.0 / 32
+    u0 = inputs.random_field(n, L, seed=9, rms=0.2)
+    xw0, tri, seq, win = _wing_window(n, L, K, 120, u0, torch.float64, dt)
+    g = Solver(n, L, nu, eta, dt, precision="fp64", with_adjoint=True)
+    x = dev(xw0, torch.float64).requires_grad_(True)
+    out = TimeAveragedForce.apply(x, g, win, every)
+    out[2].backward()
+    got = x.grad.cpu().numpy()
+
+    p = S.Params(n=n, L=L, nu=nu, eta=eta, dt=dt, x0=(2.0, 2.0, 2.0))
+    masks = []
+    for xw, vw, fr in seq:
+        chi, us, _, _ = OM.rasterise(n, L, xw, vw, tri, fr, 2 * dx, 1.5 * dx)
+        masks.append((chi, us))
+    w = np.full(K, 1.0 / K)
+    a, b = np.array([0.0, 0.0, 1.0]), np.zeros(3)
+    J, states = OA.forward(p, u0, masks, w, a, b)
+    gchi, gus = OA.adjoint(p, states, masks, w, a, b)
+    ref = np.zeros_like(xw0)
+    for k, (xw, vw, fr) in enumerate(seq):
+        ref += OA.rasterise_vjp(n, L, xw, vw, tri, fr, 2 * dx, 1.5 * dx, gchi[k], gus[k])
+    assert abs(float(out[2]) - J) < 1e-12 * abs(J)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print("32^3 node gradient vs oracle: rel %.2e" % err)
+    assert err < 1e-9
+
+
+def test_adjoint_config_128_fp32_vs_central_differences():
+    """128^3 revolving wing (600 nodes), 64-step window with a checkpoint
+    every 8 steps: d(mean lift)/d(node positions) by the FP32 forward and
+    adjoint, against the FP64 adjoint (precision) and against central
+    differences (h = 1e-4) of the FP64 forward on 10 seeded nodes.
+
+    At this resolution many band points sit within h of a switch of their
+    closest feature (Voronoi regions of the triangles' faces, edges and
+    vertices), where the objective is only piecewise smooth; the central
+    differences then straddle kinks and differ from the exact discrete
+    derivative by about 2 % in norm for the FP64 adjoint as much as for the
+    FP32 one (measured 2.1e-2 and 2.3e-2). Exactness of the adjoint itself
+    is pinned by the 32^3 comparison with the oracle gradient."""
+    n, L, nu, eta, dt = 128, 4.0, 1.0 / 1800, 1e-3, 5e-4
+    K, every, h = 64, 8, 1e-4
+    u0 = inputs.random_field(n, L, seed=128)
+    grads = {}
+    for prec, dtype in (("fp32", torch.float32), ("fp64", torch.float64)):
+        xw0, tri, seq, win = _wing_window(n, L, K, 600, u0, dtype, dt)
+        g = Solver(n, L, nu, eta, dt, precision=prec, with_adjoint=True)
+        x = dev(xw0, torch.float64).requires_grad_(True)
+        out = TimeAveragedForce.apply(x, g, win, every)
+        out[2].backward()
+        grads[prec] = x.grad.cpu().numpy()
+        g.close()
+    e_prec = np.linalg.norm(grads["fp32"] - grads["fp64"]) / np.linalg.norm(grads["fp64"])
+
+    g64 = Solver(n, L, nu, eta, dt, precision="fp64")
+
+    def J(xw):
+        with torch.no_grad():
+            return float(TimeAveragedForce.apply(dev(xw, torch.float64), g64, win, every)[2])
+
+    rng = np.random.default_rng(64)
+    fd, ad = [], []
+    for node in rng.choice(len(xw0), 10, replace=False):
+        for c in range(3):
+            xp = xw0.copy(); xp[node, c] += h
+            xm = xw0.copy(); xm[node, c] -= h
+            fd.append((J(xp) - J(xm)) / (2 * h))
+            ad.append(grads["fp32"][node, c])
+    fd, ad = np.array(fd), np.array(ad)
+    e_fd = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
+    med = np.median(np.abs(ad - fd) / np.abs(fd))
+    print("128^3 node gradient: fp32 vs fp64 adjoint %.2e; fp32 adjoint vs fp64 FD: norm %.2e, median %.2e" %
+          (e_prec, e_fd, med))
+    assert e_prec < 5e-3
+    assert e_fd < 5e-2 and med < 2e-2
