@@ -211,15 +211,19 @@ def test_adjoint_config_128_fp32_vs_central_differences():
     """128^3 revolving wing (600 nodes), 64-step window with a checkpoint
     every 8 steps: d(mean lift)/d(node positions) by the FP32 forward and
     adjoint, against the FP64 adjoint (precision) and against central
-    differences (h = 1e-4) of the FP64 forward on 10 seeded nodes.
+    differences (h = 1e-4) of the FP64 forward.
 
-    At this resolution many band points sit within h of a switch of their
-    closest feature (Voronoi regions of the triangles' faces, edges and
-    vertices), where the objective is only piecewise smooth; the central
-    differences then straddle kinks and differ from the exact discrete
-    derivative by about 2 % in norm for the FP64 adjoint as much as for the
-    FP32 one (measured 2.1e-2 and 2.3e-2). Exactness of the adjoint itself
-    is pinned by the 32^3 comparison with the oracle gradient."""
+    The objective is only piecewise smooth in the node positions: a band
+    point's closest feature (face, edge or vertex region of a triangle)
+    switches at kinks, and a difference quotient that straddles one differs
+    from the derivative. At this resolution most node coordinates have such
+    a switch within h somewhere in the window (over all 60 sampled ones the
+    FP64 adjoint differs from the differences by ~1 % in norm). The
+    comparison therefore uses the coordinates whose differences at h and
+    h/2 agree to 1e-5 (no kink in reach; 5 of 60 here), where the FP64
+    adjoint must match to 2e-4 (measured 6.9e-5) and the FP32 adjoint to
+    1e-2 (measured 4.8e-3); exactness of the adjoint itself is pinned by the
+    32^3 comparison with the oracle gradient."""
     n, L, nu, eta, dt = 128, 4.0, 1.0 / 1800, 1e-3, 5e-4
     K, every, h = 64, 8, 1e-4
     u0 = inputs.random_field(n, L, seed=128)
@@ -240,18 +244,27 @@ def test_adjoint_config_128_fp32_vs_central_differences():
         with torch.no_grad():
             return float(TimeAveragedForce.apply(dev(xw, torch.float64), g64, win, every)[2])
 
-    rng = np.random.default_rng(64)
-    fd, ad = [], []
-    for node in rng.choice(len(xw0), 10, replace=False):
+    def fd(node, c, hh):
+        xp = xw0.copy(); xp[node, c] += hh
+        xm = xw0.copy(); xm[node, c] -= hh
+        return (J(xp) - J(xm)) / (2 * hh)
+
+    rng = np.random.default_rng(7)
+    rows = []
+    for node in rng.choice(len(xw0), 20, replace=False):
         for c in range(3):
-            xp = xw0.copy(); xp[node, c] += h
-            xm = xw0.copy(); xm[node, c] -= h
-            fd.append((J(xp) - J(xm)) / (2 * h))
-            ad.append(grads["fp32"][node, c])
-    fd, ad = np.array(fd), np.array(ad)
-    e_fd = np.linalg.norm(ad - fd) / np.linalg.norm(fd)
-    med = np.median(np.abs(ad - fd) / np.abs(fd))
-    print("128^3 node gradient: fp32 vs fp64 adjoint %.2e; fp32 adjoint vs fp64 FD: norm %.2e, median %.2e" %
-          (e_prec, e_fd, med))
+            f1, f2 = fd(node, c, h), fd(node, c, h / 2)
+            rows.append((f1, f2, grads["fp64"][node, c], grads["fp32"][node, c]))
+    rows = np.array(rows)
+    f1, f2, a64, a32 = rows.T
+    smooth = np.abs(f1 - f2) <= 1e-5 * np.abs(f1) + 1e-10
+    e_all = np.linalg.norm(a64 - f1) / np.linalg.norm(f1)
+    e64 = np.abs(a64 - f2)[smooth] / np.abs(f2)[smooth]
+    e32 = np.abs(a32 - f2)[smooth] / np.abs(f2)[smooth]
+    print("128^3 node gradient: fp32 vs fp64 adjoint %.2e; fp64 adjoint vs FD over all %d coords %.2e; "
+          "%d kink-free coords: fp64 max %.2e, fp32 max %.2e" %
+          (e_prec, len(f1), e_all, smooth.sum(), e64.max() if smooth.any() else -1, e32.max() if smooth.any() else -1))
     assert e_prec < 5e-3
-    assert e_fd < 5e-2 and med < 2e-2
+    assert smooth.sum() >= 3
+    assert e64.max() < 2e-4
+    assert e32.max() < 1e-2
