@@ -79,10 +79,6 @@
 #ifndef PS_X1_SMEM_KB
 #define PS_X1_SMEM_KB 64
 #endif
-// x-forward update: points per thread whose U/H loads are issued together
-#ifndef PS_X5_UNR
-#define PS_X5_UNR 1
-#endif
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
 #endif
@@ -1151,8 +1147,9 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
     constexpr int NBK = GE::nbox(K), BRK = GE::brows(K);
     for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
         const int cy = t / NTZ, czt = t % NTZ;
-        // U and H of this tile are read only after the three transforms:
-        // start pulling them into L2 now
+        // U (first step) or Q of this tile is read only after the three
+        // transforms: start pulling it into L2 now (measured: loading it into
+        // registers here instead, held across the transforms, was slower)
         if (MODE == 0 && threadIdx.x < 3 * NBK) {
             const int f = threadIdx.x / NBK, b = threadIdx.x % NBK;
             tma_prefetch_2d(first ? &tmu : &tmh, 2 * czt * CT, (f * K + cy) * K + b * BRK);
@@ -1225,43 +1222,33 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             }
             nn[0] = n0; nn[1] = n1; nn[2] = n2;
         };
-        constexpr int UNR = MODE == 0 ? PS_X5_UNR : 1;
-        for (int i0 = threadIdx.x; i0 < K * CT; i0 += UNR * blockDim.x) {
-            // the U (and H) loads of UNR points first, then their updates
-            C2 uq[UNR][3];
-            bool okp[UNR];
+        // points per thread: every load of a point issued before its arithmetic
+        constexpr int NT = CT * G, NPT = (K * CT + NT - 1) / NT;
 #pragma unroll
-            for (int r = 0; r < UNR; ++r) {
-                const int idx = i0 + r * blockDim.x;
-                const int cx = idx / CT, czz = czt * CT + idx % CT;
-                okp[r] = idx < K * CT && czz < Kz;
-                if (MODE == 0 && okp[r]) {
-                    const size_t o = ((size_t)cy * K + cx) * KZP + czz;
+        for (int r = 0; r < NPT; ++r) {
+            const int idx = threadIdx.x + r * NT;
+            const int cx = idx / CT, czz = czt * CT + idx % CT;
+            if (idx >= K * CT || czz >= Kz) continue;
+            const size_t o = ((size_t)cy * K + cx) * KZP + czz;
+            C2 uq[3];
+            if constexpr (MODE == 0) {
 #pragma unroll
-                    for (int ff = 0; ff < 3; ++ff) uq[r][ff] = first ? U[ff * FS + o] : H[ff * FS + o];
-                }
+                for (int ff = 0; ff < 3; ++ff) uq[ff] = first ? U[ff * FS + o] : H[ff * FS + o];
             }
+            C2 nn[3];
+            proj(idx, cx, czz, nn);
+            if constexpr (MODE == 1) {
+                U[o] = nn[0]; U[FS + o] = nn[1]; U[2 * FS + o] = nn[2];
+                const C2 z = cmk<C2>((T)0, (T)0);
+                H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
+            } else {
+                const T E = Ex[cx] * ey * Ez[czz];
 #pragma unroll
-            for (int r = 0; r < UNR; ++r) {
-                if (!okp[r]) continue;
-                const int idx = i0 + r * blockDim.x;
-                const int cx = idx / CT, czz = czt * CT + idx % CT;
-                C2 nn[3];
-                proj(idx, cx, czz, nn);
-                const size_t o = ((size_t)cy * K + cx) * KZP + czz;
-                if constexpr (MODE == 1) {
-                    U[o] = nn[0]; U[FS + o] = nn[1]; U[2 * FS + o] = nn[2];
-                    const C2 z = cmk<C2>((T)0, (T)0);
-                    H[o] = z; H[FS + o] = z; H[2 * FS + o] = z;
-                } else {
-                    const T E = Ex[cx] * ey * Ez[czz];
-#pragma unroll
-                    for (int ff = 0; ff < 3; ++ff) {
-                        C2 un, qn;
-                        ab2_update(uq[r][ff], nn[ff], E, dt, first != 0, un, qn);
-                        U[ff * FS + o] = un;
-                        H[ff * FS + o] = qn;
-                    }
+                for (int ff = 0; ff < 3; ++ff) {
+                    C2 un, qn;
+                    ab2_update(uq[ff], nn[ff], E, dt, first != 0, un, qn);
+                    U[ff * FS + o] = un;
+                    H[ff * FS + o] = qn;
                 }
             }
         }
