@@ -132,39 +132,48 @@ __global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w
                             const T* __restrict__ chi, const T* __restrict__ us, T* __restrict__ gchi,
                             T* __restrict__ gus, int n) {
     const size_t n3 = (size_t)n * n * n;
-    const double inv_eta = kp.inv_eta;
-    const double fw = kp.dx * kp.dx * kp.dx * inv_eta;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (size_t)gridDim.x * blockDim.x) {
-        const T nbx = nb[p] * (T)kp.invn3, nby = nb[n3 + p] * (T)kp.invn3, nbz = nb[2 * n3 + p] * (T)kp.invn3;
-        const T ux = u[p], uy = u[n3 + p], uz = u[2 * n3 + p];
-        const T wx = w[p], wy = w[n3 + p], wz = w[2 * n3 + p];
-        const T c = chi[p];
-        const T ce = c * (T)inv_eta;
-        // ubar = w x nbar - c nbar ; wbar = nbar x u
-        T bx = wy * nbz - wz * nby - ce * nbx;
-        T by = wz * nbx - wx * nbz - ce * nby;
-        T bz = wx * nby - wy * nbx - ce * nbz;
-        const T vx = nby * uz - nbz * uy;
-        const T vy = nbz * ux - nbx * uz;
-        const T vz = nbx * uy - nby * ux;
-        // dJ/dchi is needed at every cell (also where chi = 0); the force and
-        // moment term uses dJ/dp = a + b x r, p = chi (u - us)
-        const T sx = us[p], sy = us[n3 + p], sz = us[2 * n3 + p];
-        const T dx_ = ux - sx, dy_ = uy - sy, dz_ = uz - sz;
-        const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / ((size_t)n * n));
-        const T rx = (T)(i * kp.dx - kp.x0[0]), ry = (T)(j * kp.dx - kp.x0[1]), rz = (T)(k * kp.dx - kp.x0[2]);
-        const T gx = (T)aw.a[0] + (T)aw.b[1] * rz - (T)aw.b[2] * ry;
-        const T gy = (T)aw.a[1] + (T)aw.b[2] * rx - (T)aw.b[0] * rz;
-        const T gz = (T)aw.a[2] + (T)aw.b[0] * ry - (T)aw.b[1] * rx;
-        const T f = (T)fw;
-        const T cf = f * c;
-        bx += cf * gx; by += cf * gy; bz += cf * gz;
-        const T gc = -(T)inv_eta * (nbx * dx_ + nby * dy_ + nbz * dz_) + f * (gx * dx_ + gy * dy_ + gz * dz_);
-        const T gsx = ce * nbx - cf * gx, gsy = ce * nby - cf * gy, gsz = ce * nbz - cf * gz;
-        u[p] = bx; u[n3 + p] = by; u[2 * n3 + p] = bz;
-        w[p] = vx; w[n3 + p] = vy; w[2 * n3 + p] = vz;
-        gchi[p] = gc;
-        gus[p] = gsx; gus[n3 + p] = gsy; gus[2 * n3 + p] = gsz;
+    // constants in T: no double arithmetic and no 64-bit division per point
+    const T inv_eta = (T)kp.inv_eta, invn3 = (T)kp.invn3, dx = (T)kp.dx;
+    const T f = (T)(kp.dx * kp.dx * kp.dx * kp.inv_eta);
+    const T x0 = (T)kp.x0[0], y0 = (T)kp.x0[1], z0 = (T)kp.x0[2];
+    const T a0 = (T)aw.a[0], a1 = (T)aw.a[1], a2 = (T)aw.a[2];
+    const T b0 = (T)aw.b[0], b1 = (T)aw.b[1], b2 = (T)aw.b[2];
+    // 32-bit point index (n^3 < 2^32 for every built grid size)
+    const uint32_t n3u = (uint32_t)n3, un = (uint32_t)n;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n3u; p += gridDim.x * blockDim.x) {
+        {
+            const uint32_t q = p / un, k = p - q * un;
+            const uint32_t i = q / un, j = q - i * un;
+            const T rx = (T)i * dx - x0, ry = (T)j * dx - y0;
+            const T nbx = nb[p] * invn3, nby = nb[n3 + p] * invn3, nbz = nb[2 * n3 + p] * invn3;
+            const T ux = u[p], uy = u[n3 + p], uz = u[2 * n3 + p];
+            const T wx = w[p], wy = w[n3 + p], wz = w[2 * n3 + p];
+            const T c = chi[p];
+            const T ce = c * inv_eta;
+            // ubar = w x nbar - c nbar ; wbar = nbar x u
+            T bx = wy * nbz - wz * nby - ce * nbx;
+            T by = wz * nbx - wx * nbz - ce * nby;
+            T bz = wx * nby - wy * nbx - ce * nbz;
+            const T vx = nby * uz - nbz * uy;
+            const T vy = nbz * ux - nbx * uz;
+            const T vz = nbx * uy - nby * ux;
+            // dJ/dchi is needed at every cell (also where chi = 0); the force
+            // and moment term uses dJ/dp = a + b x r, p = chi (u - us)
+            const T sx = us[p], sy = us[n3 + p], sz = us[2 * n3 + p];
+            const T dx_ = ux - sx, dy_ = uy - sy, dz_ = uz - sz;
+            const T rz = (T)k * dx - z0;
+            const T gx = a0 + b1 * rz - b2 * ry;
+            const T gy = a1 + b2 * rx - b0 * rz;
+            const T gz = a2 + b0 * ry - b1 * rx;
+            const T cf = f * c;
+            bx += cf * gx; by += cf * gy; bz += cf * gz;
+            const T gc = -inv_eta * (nbx * dx_ + nby * dy_ + nbz * dz_) + f * (gx * dx_ + gy * dy_ + gz * dz_);
+            const T gsx = ce * nbx - cf * gx, gsy = ce * nby - cf * gy, gsz = ce * nbz - cf * gz;
+            u[p] = bx; u[n3 + p] = by; u[2 * n3 + p] = bz;
+            w[p] = vx; w[n3 + p] = vy; w[2 * n3 + p] = vz;
+            gchi[p] = gc;
+            gus[p] = gsx; gus[n3 + p] = gsy; gus[2 * n3 + p] = gsz;
+        }
     }
 }
 

@@ -411,7 +411,15 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
     if ((e = c->ops->inv3(c->kp, c->b, c->b.U, up, s)) != cudaSuccess) return e;
     if ((e = c->ops->inv3(c->kp, c->b, W, wp, s)) != cudaSuccess) return e;
     if ((e = c->ops->inv3(c->kp, c->b, G, np_, s)) != cudaSuccess) return e;
-    k_adj_point<T><<<nb * 2, 256, 0, s>>>(c->kp, aw, up, wp, np_, (const T*)c->b.chi, (const T*)c->b.us, (T*)gchi,
+    // grid-stride pointwise pass: exactly the blocks that are resident at once
+    static int pt_blocks = 0;
+    if (pt_blocks == 0) {
+        int occ = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_point<T>, 256, 0);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        pt_blocks = (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+    }
+    k_adj_point<T><<<pt_blocks, 256, 0, s>>>(c->kp, aw, up, wp, np_, (const T*)c->b.chi, (const T*)c->b.us, (T*)gchi,
                                           (T*)gus, c->p.n);
     if ((e = c->ops->fwd3(c->kp, c->b, up, Ub, s)) != cudaSuccess) return e;
     if ((e = c->ops->fwd3(c->kp, c->b, wp, Wb, s)) != cudaSuccess) return e;

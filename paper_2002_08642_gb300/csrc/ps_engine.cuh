@@ -75,7 +75,7 @@ template <typename T, int N> struct Engine {
     static constexpr size_t tw_bytes = (size_t)GE::tw_n * sizeof(C2);
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
-    static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2);
+    static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2) / 2;
     static constexpr size_t sm_zp = (size_t)GE::zsmem(GE::LZ);
     static constexpr int thr_s = GE::C * GE::G;
     static constexpr int thr_5 = GE::C5 * GE::G;

@@ -61,6 +61,11 @@
 #ifndef PS_ZWS
 #define PS_ZWS 1
 #endif
+// lines per block of the physical <-> z-spectral kernels: shared-memory
+// budget in KiB for twice their tiles
+#ifndef PS_LY_SMEM_KB
+#define PS_LY_SMEM_KB 64
+#endif
 // tile width of the TMA-staged y passes (0 = automatic)
 #ifndef PS_TY_C
 #define PS_TY_C 0
@@ -153,12 +158,12 @@ template <typename T, int N> struct Geo {
     static constexpr int ly_threads() { int l = 256 / G; return l < 1 ? 1 : l; }
     static constexpr int ly_smem() {
         int l = 1;
-        while (l * 2 * 3 * LP * (int)sizeof(C2) <= 64 * 1024) l *= 2;
+        while (l * 2 * 3 * LP * (int)sizeof(C2) <= PS_LY_SMEM_KB * 1024) l *= 2;
         return l;
     }
     static constexpr int LYa = ly_threads() < ly_smem() ? ly_threads() : ly_smem();
     static constexpr int ly_fix(int l) { while (l > 1 && (N * N) % l != 0) l /= 2; return l; }
-    static constexpr int LY = ly_fix(LYa);
+    static constexpr int LY = ly_fix(LYa) < 2 ? 2 : ly_fix(LYa);   // even: z lines are paired
     // kept z modes, padded to the tile width
     static constexpr int KZ = (N - 1) / 3 + 1;
     static constexpr int KZP = (KZ + CW - 1) / CW * CW;
@@ -1257,6 +1262,9 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
 }
 
 // ----------------------------------------------- physical <-> z-spectral
+// LY z lines per block, G threads per line (one warp or less: warp barriers
+// between FFT stages). Each line's (u_x + i u_y) is one complex transform;
+// u_z of lines 2m and 2m + 1 share one, (u_z[2m] + i u_z[2m+1]).
 // Forward: physical u (3 x n^3 real) -> B fields 0..2 (z r2c, kz < Kz).
 template <typename T, int N>
 __global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
@@ -1264,9 +1272,13 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    static_assert(LY % 2 == 0, "z lines come in pairs");
+    constexpr bool WS = G <= 32 && 32 % G == 0;
+    using FFT = LineFFT<T, N, -1, WS>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* tiles = tw + GE::tw_n;
+    C2* t0 = tw + GE::tw_n;          // [LY][LP]: (u_x + i u_y) of each line
+    C2* t1 = t0 + LY * LP;           // [LY / 2][LP]: u_z of each line pair
     const int line = threadIdx.x / G, g = threadIdx.x % G;
     const long lid = (long)blockIdx.x * LY + line;
     const int x = (int)(lid / N), y = (int)(lid % N);
@@ -1276,31 +1288,35 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
     const size_t N3 = (size_t)N * N * N;
     const size_t po = ((size_t)x * N + y) * N;
     load_tw(tw, twg, GE::tw_n);
-    auto addr = [&](int p) { return zaddr(p, line, LP); };
-    C2* t0 = tiles;
-    C2* t1 = tiles + LY * LP;
     __syncthreads();
     {
+        auto addr = [&](int p) { return zaddr(p, line, LP); };
         auto load = [&](int z) -> C2 { return cmk<C2>(u[po + z], u[N3 + po + z]); };
         auto store = [&](int p, C2 v) { t0[addr(p)] = v; };
-        LineFFT<T, N, -1>::template run<false>(t0, tw, addr, g, load, store);
+        FFT::template run<false>(t0, tw, addr, g, load, store);
     }
-    __syncthreads();
     {
-        auto load = [&](int z) -> C2 { return cmk<C2>(u[2 * N3 + po + z], (T)0); };
+        const bool even = (line & 1) == 0;
+        auto addr = [&](int p) { return zaddr(p, line >> 1, LP); };
+        auto load = [&](int z) -> C2 { return cmk<C2>(u[2 * N3 + po + z], u[2 * N3 + po + N + z]); };
         auto store = [&](int p, C2 v) { t1[addr(p)] = v; };
-        LineFFT<T, N, -1>::template run<false>(t1, tw, addr, g, load, store);
+        FFT::template run_masked<false>(t1, tw, addr, g, load, store, even);
     }
     __syncthreads();
     C2* o0 = B + lo;
     C2* o1 = B + BS + lo;
     C2* o2 = B + 2 * BS + lo;
+    const C2* w1 = t1 + (line >> 1) * LP;
     for (int k = g; k < Kz; k += G) {
-        const C2 zk = t0[addr(k)];
-        const C2 zm = t0[addr((N - k) % N)];
+        const int m = (N - k) % N;
+        const C2 zk = t0[zaddr(k, line, LP)];
+        const C2 zm = t0[zaddr(m, line, LP)];
+        // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
         o0[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
         o1[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
-        o2[k] = t1[addr(k)];
+        const C2 wk = w1[k + (k >> 4)], wm = w1[m + (m >> 4)];
+        o2[k] = (line & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
+                           : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
     }
 }
 
@@ -1311,9 +1327,12 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    static_assert(LY % 2 == 0, "z lines come in pairs");
+    constexpr bool WS = G <= 32 && 32 % G == 0;
+    using FFT = LineFFT<T, N, 1, WS>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* tiles = tw + GE::tw_n;
+    C2* tiles = tw + GE::tw_n;       // [LY][LP], reused by the two transforms
     const int line = threadIdx.x / G, g = threadIdx.x % G;
     const long lid = (long)blockIdx.x * LY + line;
     const int x = (int)(lid / N), y = (int)(lid % N);
@@ -1325,31 +1344,32 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     load_tw(tw, twg, GE::tw_n);
     auto addr = [&](int p) { return zaddr(p, line, LP); };
     __syncthreads();
-#pragma unroll 1
-    for (int pr = 0; pr < 2; ++pr) {
-        C2* tp = tiles + pr * LY * LP;
-        const C2* fa = B + (2 * pr) * BS + lo;
-        const C2* fb = B + (2 * pr + 1) * BS + lo;
-        const bool pair = (pr == 0);
-        auto load = [&](int q) -> C2 {
-            if (q < Kz) {
-                C2 a = fa[q];
-                C2 b = pair ? fb[q] : cmk<C2>((T)0, (T)0);
-                if (q == 0) { a.y = 0; b.y = 0; }
-                return cmk<C2>(a.x - b.y, a.y + b.x);
-            }
-            if (q > N - Kz) {
-                C2 a = fa[N - q];
-                C2 b = pair ? fb[N - q] : cmk<C2>((T)0, (T)0);
-                return cmk<C2>(a.x + b.y, b.x - a.y);
-            }
-            return cmk<C2>((T)0, (T)0);
-        };
-        auto store = [&](int z, C2 v) {
-            if (pair) { u[po + z] = v.x; u[N3 + po + z] = v.y; }
-            else u[2 * N3 + po + z] = v.x;
-        };
-        LineFFT<T, N, 1>::template run<false>(tp, tw, addr, g, load, store);
+    // (A + i B) of two real lines from their half spectra a, b
+    auto two = [&](const C2* fa, const C2* fb, int q) -> C2 {
+        if (q < Kz) {
+            C2 a = fa[q], b = fb[q];
+            if (q == 0) { a.y = 0; b.y = 0; }
+            return cmk<C2>(a.x - b.y, a.y + b.x);
+        }
+        if (q > N - Kz) {
+            const C2 a = fa[N - q], b = fb[N - q];
+            return cmk<C2>(a.x + b.y, b.x - a.y);
+        }
+        return cmk<C2>((T)0, (T)0);
+    };
+    {
+        auto load = [&](int q) -> C2 { return two(B + lo, B + BS + lo, q); };
+        auto store = [&](int z, C2 v) { u[po + z] = v.x; u[N3 + po + z] = v.y; };
+        FFT::template run<false>(tiles, tw, addr, g, load, store);
+    }
+    // the tile is reused: every thread of the line is past the last stage
+    if constexpr (WS) __syncwarp(warp_lanes());
+    else __syncthreads();
+    {
+        const C2* f2 = B + 2 * BS + lo;
+        auto load = [&](int q) -> C2 { return two(f2, f2 + Kzp, q); };
+        auto store = [&](int z, C2 v) { u[2 * N3 + po + z] = v.x; u[2 * N3 + po + N + z] = v.y; };
+        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, (line & 1) == 0);
     }
 }
 
