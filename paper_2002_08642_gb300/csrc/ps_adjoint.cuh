@@ -70,31 +70,6 @@ __global__ void k_adj_spec1(KP kp, cplx<T>* __restrict__ lam, cplx<T>* __restric
     }
 }
 
-// W = i k x U (compact arrays), or W += i k x U scaled (accumulate form).
-template <typename T>
-__global__ void k_curl_spec(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ W) {
-    using C2 = cplx<T>;
-    const int K = kp.K, Kz = kp.Kz, Kzp = kp.Kzp, mm = kp.mmax;
-    const size_t FS = (size_t)K * K * Kzp;
-    const size_t tot = (size_t)K * K * Kz;
-    const T s = (T)kp.ks;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const int cz = (int)(i % Kz);
-        const size_t r = i / Kz;
-        const int cx = (int)(r % K), cy = (int)(r / K);
-        const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
-        const T kx = s * (T)cmode_of(cx, mm, K), ky = s * (T)cmode_of(cy, mm, K), kz = s * (T)cz;
-        const C2 ux = U[o], uy = U[FS + o], uz = U[2 * FS + o];
-        // i (k x u)
-        const C2 cx_ = cmk<C2>(ky * uz.x - kz * uy.x, ky * uz.y - kz * uy.y);
-        const C2 cy_ = cmk<C2>(kz * ux.x - kx * uz.x, kz * ux.y - kx * uz.y);
-        const C2 cz_ = cmk<C2>(kx * uy.x - ky * ux.x, kx * uy.y - ky * ux.y);
-        W[o] = cmk<C2>(-cx_.y, cx_.x);
-        W[FS + o] = cmk<C2>(-cy_.y, cy_.x);
-        W[2 * FS + o] = cmk<C2>(-cz_.y, cz_.x);
-    }
-}
-
 // lam += n^3 (Ub + i k x Wb).
 template <typename T>
 __global__ void k_adj_spec2(KP kp, cplx<T>* __restrict__ lam, const cplx<T>* __restrict__ Ub,

@@ -105,7 +105,8 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->err = take(256);
     L->mask_bytes = mask_workspace_bytes(n);
     L->mask = take(L->mask_bytes);
-    for (int i = 0; i < 6; ++i) L->adj_spec[i] = p->with_adjoint ? take(L->ustate) : 0;
+    // lam, mu, G, (unused), Ub, Wb
+    for (int i = 0; i < 6; ++i) L->adj_spec[i] = p->with_adjoint && i != 3 ? take(L->ustate) : 0;
     for (int i = 0; i < 3; ++i) L->adj_phys[i] = p->with_adjoint ? take(3 * n3 * er) : 0;
     L->gX = take((size_t)kMaskMaxNodes * 3 * sizeof(double));
     L->total = off;
@@ -399,7 +400,6 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
     C2* lam = (C2*)c->adj_spec[0];
     C2* mu = (C2*)c->adj_spec[1];
     C2* G = (C2*)c->adj_spec[2];
-    C2* W = (C2*)c->adj_spec[3];
     C2* Ub = (C2*)c->adj_spec[4];
     C2* Wb = (C2*)c->adj_spec[5];
     T* up = (T*)c->adj_phys[0];
@@ -407,9 +407,7 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
     T* np_ = (T*)c->adj_phys[2];
     cudaError_t e;
     k_adj_spec1<T><<<nb, 256, 0, s>>>(c->kp, lam, mu, G, (const T*)c->b.Ex, (const T*)c->b.Ez, aw.first);
-    k_curl_spec<T><<<nb, 256, 0, s>>>(c->kp, (const C2*)c->b.U, W);
-    if ((e = c->ops->inv3(c->kp, c->b, c->b.U, up, s)) != cudaSuccess) return e;
-    if ((e = c->ops->inv3(c->kp, c->b, W, wp, s)) != cudaSuccess) return e;
+    if ((e = c->ops->inv_uw(c->kp, c->b, up, wp, s)) != cudaSuccess) return e;
     if ((e = c->ops->inv3(c->kp, c->b, G, np_, s)) != cudaSuccess) return e;
     // grid-stride pointwise pass: exactly the blocks that are resident at once
     static int pt_blocks = 0;
@@ -507,7 +505,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     c->out = (double*)(w + L.out);
     c->b.err = (int*)(w + L.err);
     c->mask_ws = w + L.mask;
-    for (int i = 0; i < 6; ++i) c->adj_spec[i] = p->with_adjoint ? (void*)(w + L.adj_spec[i]) : nullptr;
+    for (int i = 0; i < 6; ++i) c->adj_spec[i] = p->with_adjoint && i != 3 ? (void*)(w + L.adj_spec[i]) : nullptr;
     for (int i = 0; i < 3; ++i) c->adj_phys[i] = p->with_adjoint ? (void*)(w + L.adj_phys[i]) : nullptr;
     c->gX = (double*)(w + L.gX);
     c->mask_ws_bytes = L.mask_bytes;

@@ -67,6 +67,8 @@ struct Ops {
     // [ky][kx][kz]) and physical arrays (3 x n^3); A, B are used as scratch
     cudaError_t (*inv3)(const KP&, const Bufs&, const void* spec, void* phys, cudaStream_t);
     cudaError_t (*fwd3)(const KP&, const Bufs&, const void* phys, void* spec, cudaStream_t);
+    // physical u and omega of the state in U (A, B used as scratch)
+    cudaError_t (*inv_uw)(const KP&, const Bufs&, void* u, void* w, cudaStream_t);
 };
 
 template <typename T, int N> struct Engine {
@@ -163,6 +165,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_xinv_tma<T, N>, sm_x1))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N>, thr_x1, sm_x1))) return e;
         x1grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
@@ -273,10 +276,26 @@ template <typename T, int N> struct Engine {
 
     static cudaError_t fwd3(const KP& kp, const Bufs& b, const void* phys, void* spec, cudaStream_t s) {
         const C2* tw = (const C2*)b.tw;
-        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)phys, (C2*)b.B, tw);
-        k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
-        k_xfwd<T, N, 2><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)spec, nullptr,
-                                                                 (const T*)b.Ex, (const T*)b.Ez, 0, tw);
+        KP k1 = kp;
+        k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const T*)phys, (C2*)b.B, tw);
+        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        k_xfwd_tma<T, N, 2><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, (C2*)spec, nullptr,
+                                                            (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
+        return cudaGetLastError();
+    }
+
+    // u and omega = curl u of the state U, physical (3 x n^3 each): the
+    // step's x (curl fused) and y passes, then z c2r of fields 0..2 and 3..5
+    static cudaError_t inv_uw(const KP& kp, const Bufs& b, void* u, void* w, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        KP k1 = kp;
+        k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
+        k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        const size_t BS = (size_t)N * N * k1.Kzp;
+        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, tw);
+        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, tw);
         return cudaGetLastError();
     }
 
@@ -294,6 +313,7 @@ template <typename T, int N> struct Engine {
         o.get_velocity = &get_velocity;
         o.inv3 = &inv3;
         o.fwd3 = &fwd3;
+        o.inv_uw = &inv_uw;
         return o;
     }
 };

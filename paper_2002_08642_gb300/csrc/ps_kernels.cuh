@@ -1097,9 +1097,10 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 // pass 5 (TMA-staged): x-forward of the three fields of n, truncation to the
 // kept kx, 1/n^3, Leray projection and the integrating-factor AB2 (Euler on
 // the first step) update of U and H. MODE 1 instead sets U to the projected
-// field (mean kept) and clears H. Each field is transformed in place in its
-// staging buffer; kept outputs go to three result tiles.
-// tm: A as 3-D {2 Kzp reals, K (cy), 3 n (f n + x)}.
+// field (mean kept) and clears H; MODE 2 writes the truncated transform
+// times 1/n^3 to U (no projection; H unused). Each field is transformed in
+// place in its staging buffer; kept outputs go to three result tiles.
+// tm: A as rows of 2 Kzp reals, row (f K + ky) n + x.
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(Geo<T, N>::CX5 * Geo<T, N>::G)
 k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmu,
@@ -1239,6 +1240,14 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             if constexpr (MODE == 0) {
 #pragma unroll
                 for (int ff = 0; ff < 3; ++ff) uq[ff] = first ? U[ff * FS + o] : H[ff * FS + o];
+            }
+            if constexpr (MODE == 2) {
+#pragma unroll
+                for (int ff = 0; ff < 3; ++ff) {
+                    const C2 v = Rt[ff * K * CT + idx];
+                    U[ff * FS + o] = cmk<C2>(v.x * invn3, v.y * invn3);
+                }
+                continue;
             }
             C2 nn[3];
             proj(idx, cx, czz, nn);
