@@ -43,6 +43,7 @@ struct ps_ctx {
     bool mask_dense_dirty;    // chi/u_s may be nonzero outside the touched list
     CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
     CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
+    CUtensorMap tmG;          // adjoint G (x-inverse input), with_adjoint only
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
     CUtensorMap tmBo;         // B in y-forward boxes of the slab pipeline
     // adjoint (with_adjoint): lam, mu, G, W, Ub, Wb spectral; u, w, nb physical
@@ -408,7 +409,7 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
     cudaError_t e;
     k_adj_spec1<T><<<nb, 256, 0, s>>>(c->kp, lam, mu, G, (const T*)c->b.Ex, (const T*)c->b.Ez, aw.first);
     if ((e = c->ops->inv_uw(c->kp, c->b, up, wp, s)) != cudaSuccess) return e;
-    if ((e = c->ops->inv3(c->kp, c->b, G, np_, s)) != cudaSuccess) return e;
+    if ((e = c->ops->inv_g(c->kp, c->b, np_, s)) != cudaSuccess) return e;
     // grid-stride pointwise pass: exactly the blocks that are resident at once
     static int pt_blocks = 0;
     if (pt_blocks == 0) {
@@ -543,6 +544,14 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         c->b.tmUp = &c->tmUp;
         c->b.tmHp = &c->tmHp;
         c->b.tmBo = &c->tmBo;
+        c->b.tmG = nullptr;
+        if (p->with_adjoint) {
+            if (!encode_rows(&c->tmG, c->adj_spec[2], c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2)) {
+                delete c;
+                return PS_ECUDA;
+            }
+            c->b.tmG = &c->tmG;
+        }
     }
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;

@@ -42,6 +42,7 @@ struct Bufs {
     const CUtensorMap* tmUp; // U, H as rows of 2 Kzp reals, x-forward box (L2 prefetch)
     const CUtensorMap* tmHp;
     const CUtensorMap* tmBo; // B, y-forward box of the slab pipeline
+    const CUtensorMap* tmG;  // adjoint G as rows of 2 Kzp reals, x-inverse box (null without adjoint)
     cudaStream_t aux[2];     // slab pipeline streams
     cudaEvent_t sev[3];      // fork/join events of the slab pipeline
 };
@@ -69,6 +70,8 @@ struct Ops {
     cudaError_t (*fwd3)(const KP&, const Bufs&, const void* phys, void* spec, cudaStream_t);
     // physical u and omega of the state in U (A, B used as scratch)
     cudaError_t (*inv_uw)(const KP&, const Bufs&, void* u, void* w, cudaStream_t);
+    // physical inverse of the adjoint array G (needs b.tmG)
+    cudaError_t (*inv_g)(const KP&, const Bufs&, void* phys, cudaStream_t);
 };
 
 template <typename T, int N> struct Engine {
@@ -163,6 +166,8 @@ template <typename T, int N> struct Engine {
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N, GE::CY4>, thr_y4, sm_y4))) return e;
         y4grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = attr(k_xinv_tma<T, N>, sm_x1))) return e;
+        if ((e = attr(k_xinv_tma<T, N, 3>, sm_x1))) return e;
+        if ((e = attr(k_yinv_tma<T, N, 3>, sm_y2))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
@@ -285,6 +290,18 @@ template <typename T, int N> struct Engine {
         return cudaGetLastError();
     }
 
+    // physical (3 x n^3) inverse transform of the adjoint array G (b.tmG)
+    // through the TMA x and y passes
+    static cudaError_t inv_g(const KP& kp, const Bufs& b, void* phys, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        KP k1 = kp;
+        k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+        k_xinv_tma<T, N, 3><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmG, k1, (C2*)b.A, tw, b.err);
+        k_yinv_tma<T, N, 3><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)phys, tw);
+        return cudaGetLastError();
+    }
+
     // u and omega = curl u of the state U, physical (3 x n^3 each): the
     // step's x (curl fused) and y passes, then z c2r of fields 0..2 and 3..5
     static cudaError_t inv_uw(const KP& kp, const Bufs& b, void* u, void* w, cudaStream_t s) {
@@ -314,6 +331,7 @@ template <typename T, int N> struct Engine {
         o.inv3 = &inv3;
         o.fwd3 = &fwd3;
         o.inv_uw = &inv_uw;
+        o.inv_g = &inv_g;
         return o;
     }
 };

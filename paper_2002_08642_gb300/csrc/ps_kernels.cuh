@@ -800,9 +800,11 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
 // field); each item's input tile arrives by tiled TMA copies into one of two
 // staging buffers while the previous item is transformed.
 
-// pass 2: y-inverse of the six fields, A (kept ky rows) -> B (all y rows).
-// tm: A as a 2-D array of 6 n K rows of 2 Kzp reals.
-template <typename T, int N>
+// pass 2: y-inverse of the NF (6, or 3 for a plain 3-field transform)
+// fields, A (kept ky rows) -> B (all y rows); one staging buffer, refilled
+// once the first FFT stage has read it.
+// tm: A as {2 Kzp reals, n rows (x), 6 K planes (f K + ky)}.
+template <typename T, int N, int NF = 6>
 __global__ void __launch_bounds__(Geo<T, N>::CY2 * Geo<T, N>::G)
 k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -811,7 +813,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     constexpr int CT = GE::CY2, G = GE::G, K = GE::K, KZP = GE::KZP;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
     constexpr int NTZ = KZP / CT;
-    const int NITEM = kp.xsn * NTZ * 6;   // items of this launch's x planes
+    const int NITEM = kp.xsn * NTZ * NF;  // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int NB = GE::Y2NB;
@@ -834,7 +836,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     load_tw(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int i, int buf) {  // one thread
-        const int f = i % 6, t = i / 6, x = kp.xs0 + t / NTZ, czt = t % NTZ;
+        const int f = i % NF, t = i / NF, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -858,7 +860,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             }
             break;
         }
-        const int f = i % 6, t = i / 6, x = kp.xs0 + t / NTZ, czt = t % NTZ;
+        const int f = i % NF, t = i / NF, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         const C2* Sb = S + (size_t)buf * RS * CT;
@@ -984,8 +986,10 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 //   w_x = i (ky Uz - kz Uy),  w_y = i kz Ux - Dx Uz,  w_z = Dx Uy - i ky Ux;
 // a thread keeps its last-stage outputs of Ux and Uy in registers until the
 // transforms that need them. Inputs arrive field by field (x, y, z) by TMA.
-// tm: U as 2-D rows of 2 Kzp reals, row (f K + cy) K + cx.
-template <typename T, int N>
+// NF = 3: the plain x-inverse of three fields (one transform each, no curl).
+// tm: U (or the array being transformed) as 2-D rows of 2 Kzp reals, row
+// (f K + cy) K + cx.
+template <typename T, int N, int NF = 6>
 __global__ void __launch_bounds__(Geo<T, N>::CX1 * Geo<T, N>::G)
 k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -1054,7 +1058,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             }
             const C2* Sb = S + (size_t)buf * RS * CT;
 #pragma unroll 1
-            for (int d = 0; d < (f == 0 ? 1 : 2); ++d) {
+            for (int d = 0; d < (NF == 6 && f > 0 ? 2 : 1); ++d) {
                 // d = 1: the x derivative i kx u_f
                 auto load = [&](int q) -> C2 {
                     const int m = mode_of(q, N);
@@ -1067,6 +1071,10 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                 };
                 auto store = [&](int slot, int x, C2 v) {
                     C2* o = out + GE::arow(x, cy) * KZP;
+                    if constexpr (NF == 3) {            // plain: field f only
+                        if (okz) o[f * AS] = v;
+                        return;
+                    }
                     if (f == 0) {                       // Ux
                         R1[slot] = v;
                         if (okz) o[0] = v;
