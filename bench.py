@@ -326,6 +326,26 @@ def run_ours(args, cfg):
     }
     if clk:
         out["clocks"] = clk
+    # pressure of the stepped state and its loads on the nodes (the coupling
+    # step that follows every fluid step), same workload
+    pfield = torch.empty((n, n, n), dtype=g.dtype, device=dev)
+    for _ in range(2):
+        g.pressure(pfield)
+        g.pressure_loads(pfield, xw_d[0], tri_d, frames[0])
+    torch.cuda.synchronize()
+    kp_ = max(3, args.steps // 4)
+    e0.record(stream)
+    for _ in range(kp_):
+        g.pressure(pfield)
+        g.pressure_loads(pfield, xw_d[0], tri_d, frames[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    msp = e0.elapsed_time(e1) / kp_
+    out["pressure_loads"] = {"value": n ** 3 / (msp / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_call": msp,
+                             "calls": kp_, "nodes": int(xw_d[0].shape[0]),
+                             "note": "static pressure of the state (passes 1-4, Pi_hat, one inverse field) "
+                                     "+ delta interpolation and p A/3 loads on the nodes"}
+    del pfield
     del g
     torch.cuda.empty_cache()
     if args.fp64 and world == 1:

@@ -148,6 +148,31 @@ ps_status ps_step(ps_ctx* ctx, int32_t nsteps);
  * Host outputs; synchronises the stream. */
 ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
 
+/* Static pressure p = Pi - (1/2)|u|^2 of the current state with the current
+ * mask (Sec. 4.1: Pi = p + (1/2) u.u is the total pressure of the rotational
+ * form; the fluid-solid coupling computes p^{n+1} from u^{n+1}). Pi is the
+ * gradient part the Leray projection removes from the nonlinear and
+ * penalization term N: Pi_hat = -i (k . N_hat)/|k|^2, mean zero.
+ *   p_dev  caller-owned n^3 array [x][y][z] in the context precision.
+ * Costs about one time step (the step's passes 1-4, then one inverse
+ * field). Leaves the state and the forces of ps_forces unchanged; uses the
+ * internal scratch arrays. Asynchronous. PS_ESTATE without a velocity. */
+ps_status ps_pressure(ps_ctx* ctx, void* p_dev);
+
+/* Pressure loads on the wing's mass points (Sec. 4.1, coupling paragraph):
+ * p_v = p interpolated at node v (global position X_O + R x_v) with the
+ * smoothed 4-point cosine delta (the 4-point cosine kernel convolved with
+ * the unit box, five points per axis, periodic), and
+ * F_v = -p_v sum over the triangles T containing v of (A_T/3) n_T, n_T the
+ * unit normal (b - a) x (c - a)/|...| of T's vertex order, global frame.
+ *   p_dev        n^3 pressure from ps_pressure (context precision)
+ *   xw_dev, tri_dev, frame  as in ps_set_mask_from_nodes
+ *   p_nodes_dev  n_nodes doubles out; f_nodes_dev n_nodes x 3 doubles out
+ * All device pointers caller-owned; sums in double. Asynchronous. */
+ps_status ps_pressure_loads(ps_ctx* ctx, const void* p_dev, const double* xw_dev, int32_t n_nodes,
+                            const int32_t* tri_dev, int32_t n_tri, const ps_frame* frame,
+                            double* p_nodes_dev, double* f_nodes_dev);
+
 /* Kinetic energy (1/2) int |u|^2 dV and max_k |k . c_k| of the current state
  * (c_k the Fourier coefficients), in double. Host outputs; synchronises.
  * Returns PS_ENUMERIC (and still writes the values) if the state holds a

@@ -53,6 +53,9 @@ _SIGS = {
     "ps_step": (c_int32, [c_void_p, c_int32]),
     "ps_forces": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_diagnostics": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
+    "ps_pressure": (c_int32, [c_void_p, c_void_p]),
+    "ps_pressure_loads": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, _P(PsFrame),
+                                    c_void_p, c_void_p]),
     "ps_state_size": (c_int32, [c_void_p, _P(c_size_t)]),
     "ps_save_state": (c_int32, [c_void_p, c_void_p]),
     "ps_restore_state": (c_int32, [c_void_p, c_void_p]),
@@ -164,6 +167,15 @@ def ps_forces(ctx):
     M = (c_double * 3)()
     check(lib().ps_forces(ctx, F, M), ctx)
     return list(F), list(M)
+
+
+def ps_pressure(ctx, p_ptr):
+    check(lib().ps_pressure(ctx, c_void_p(p_ptr)), ctx)
+
+
+def ps_pressure_loads(ctx, p_ptr, xw_ptr, n_nodes, tri_ptr, n_tri, frame, pn_ptr, fn_ptr):
+    check(lib().ps_pressure_loads(ctx, c_void_p(p_ptr), c_void_p(xw_ptr), n_nodes, c_void_p(tri_ptr), n_tri,
+                                  ctypes.byref(frame), c_void_p(pn_ptr), c_void_p(fn_ptr)), ctx)
 
 
 def ps_diagnostics(ctx):

@@ -17,6 +17,7 @@
 #include "ps_engine.cuh"
 #include "ps_mask.cuh"
 #include "ps_adjoint.cuh"
+#include "ps_loads.cuh"
 
 using namespace ps;
 
@@ -691,6 +692,42 @@ ps_status ps_step(ps_ctx* c, int32_t nsteps) {
         if (e != cudaSuccess) return cuda_fail(c, e, "ps_step");
         c->nstep++;
     }
+    return PS_OK;
+}
+
+ps_status ps_pressure(ps_ctx* c, void* p_dev) {
+    if (!c) return PS_EINVAL;
+    if (!p_dev) return fail(c, PS_EINVAL, "ps_pressure: null output");
+    if (!c->has_velocity) return fail(c, PS_ESTATE, "ps_pressure: no velocity set");
+    DeviceGuard dg(c->device);
+    cudaError_t e = c->ops->pressure(c->kp, c->b, p_dev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_pressure");
+    return PS_OK;
+}
+
+ps_status ps_pressure_loads(ps_ctx* c, const void* p_dev, const double* xw, int32_t n_nodes, const int32_t* tri,
+                            int32_t n_tri, const ps_frame* frame, double* p_nodes_dev, double* f_nodes_dev) {
+    if (!c) return PS_EINVAL;
+    if (!p_dev || !xw || !tri || !frame || !p_nodes_dev || !f_nodes_dev || n_nodes < 1 || n_tri < 1)
+        return fail(c, PS_EINVAL, "ps_pressure_loads: null pointer or empty mesh");
+    if (n_tri > kMaskMaxTri || n_nodes > kMaskMaxNodes)
+        return fail(c, PS_EINVAL, "ps_pressure_loads: more than 131072 triangles or nodes");
+    DeviceGuard dg(c->device);
+    LoadArgs a;
+    a.n = c->p.n;
+    a.dx = c->kp.dx;
+    a.xw = xw;
+    a.n_nodes = n_nodes;
+    a.tri = tri;
+    a.n_tri = n_tri;
+    memcpy(a.R, frame->R, sizeof(a.R));
+    memcpy(a.XO, frame->X_O, sizeof(a.XO));
+    const int nb = (n_nodes + 127) / 128;
+    if (c->fp64) k_node_pressure<double><<<nb, 128, 0, c->stream>>>(a, (const double*)p_dev, p_nodes_dev);
+    else k_node_pressure<float><<<nb, 128, 0, c->stream>>>(a, (const float*)p_dev, p_nodes_dev);
+    k_node_loads<<<nb, 128, 0, c->stream>>>(a, p_nodes_dev, f_nodes_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_pressure_loads");
     return PS_OK;
 }
 

@@ -72,6 +72,8 @@ struct Ops {
     cudaError_t (*inv_uw)(const KP&, const Bufs&, void* u, void* w, cudaStream_t);
     // physical inverse of the adjoint array G (needs b.tmG)
     cudaError_t (*inv_g)(const KP&, const Bufs&, void* phys, cudaStream_t);
+    // static pressure of the state in U with the current mask (n^3 real)
+    cudaError_t (*pressure)(const KP&, const Bufs&, void* p, cudaStream_t);
 };
 
 template <typename T, int N> struct Engine {
@@ -147,6 +149,10 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_yinv<T, N, 3>, sm_strided))) return e;
         if ((e = attr(k_yfwd<T, N>, sm_strided))) return e;
         if ((e = attr(k_zpass<T, N>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, N, true>, sm_zp))) return e;
+        if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
+        if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
+        if ((e = attr(k_zinv_phys<T, N, 1>, sm_z))) return e;
         if ((e = attr(k_zfwd_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
@@ -171,6 +177,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 3>, sm_x5t))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N>, thr_x1, sm_x1))) return e;
         x1grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
@@ -211,7 +218,7 @@ template <typename T, int N> struct Engine {
             k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
             if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
             k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                        b.flag, b.partial, tw, b.err);
+                                                        b.flag, b.partial, tw, b.err, nullptr);
             if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
             k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
             if (ev) cudaEventRecord(ev[7], s);
@@ -231,7 +238,7 @@ template <typename T, int N> struct Engine {
                 k_yinv_tma<T, N><<<ovl_y2(), thr_y2, sm_y2, st>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
                 if (e) { cudaEventRecord(e[1], st); cudaEventRecord(e[2], st); }
                 k_zpass<T, N><<<ovl_z(), thr_zp, sm_zp, st>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                             b.flag, b.partial, tw, b.err);
+                                                             b.flag, b.partial, tw, b.err, nullptr);
                 if (e) { cudaEventRecord(e[3], st); cudaEventRecord(e[4], st); }
                 k_yfwd_tma<T, N, GE::CY4O><<<ovl_y4(), thr_y4o, sm_y4o, st>>>(*b.tmBo, k1, (C2*)b.A, tw, b.err);
                 if (e) cudaEventRecord(e[5], st);
@@ -302,6 +309,28 @@ template <typename T, int N> struct Engine {
         return cudaGetLastError();
     }
 
+    // static pressure p = Pi - (1/2)|u|^2 of the state U with the current
+    // mask (n^3, [x][y][z]): the step's passes 1-4 (the z pass also writing
+    // (1/2)|u|^2 to p), the x-forward pass writing Pi_hat into A's field 3,
+    // then its inverse (x, y, then z pairs of lines: p := Pi - p)
+    static cudaError_t pressure(const KP& kp, const Bufs& b, void* p, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        KP k1 = kp;
+        k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
+        k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        k_zpass<T, N, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+                                                          b.partial, tw, b.err, (T*)p);
+        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * GE::KZP;
+        k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
+                                                            (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
+        k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
+        k_yinv<T, N, 1><<<grid_ys(k1), thr_s, sm_strided, s>>>(k1, (const C2*)b.A, (C2*)b.B, tw);
+        k_zinv_phys<T, N, 1><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)p, tw);
+        return cudaGetLastError();
+    }
+
     // u and omega = curl u of the state U, physical (3 x n^3 each): the
     // step's x (curl fused) and y passes, then z c2r of fields 0..2 and 3..5
     static cudaError_t inv_uw(const KP& kp, const Bufs& b, void* u, void* w, cudaStream_t s) {
@@ -332,6 +361,7 @@ template <typename T, int N> struct Engine {
         o.fwd3 = &fwd3;
         o.inv_uw = &inv_uw;
         o.inv_g = &inv_g;
+        o.pressure = &pressure;
         return o;
     }
 };

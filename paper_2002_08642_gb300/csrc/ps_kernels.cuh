@@ -419,11 +419,13 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // F_b the forward length-M transform of z[3a + b]; sub-line b of a tile
 // holds z[3a + b] at position b M + a, so the pointwise phase reads and
 // writes in place and no reordering pass is needed.
-template <typename T, int N>
+// PM (pressure evaluation): also writes (1/2)|u|^2 to half_u2 (n^3,
+// [x][y][z]) and leaves the force partials of the last step untouched.
+template <typename T, int N, bool PM = false>
 __global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
         const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
-        int* __restrict__ err) {
+        int* __restrict__ err, T* __restrict__ half_u2) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
@@ -555,6 +557,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             nx = uy * wz - uz * wy;
             ny = uz * wx - ux * wz;
             nz = ux * wy - uy * wx;
+            if constexpr (PM) half_u2[(size_t)lid * N + z] = (T)0.5 * (ux * ux + uy * uy + uz * uz);
             if (flag[lid] != 0) {
                 const size_t po = (size_t)lid * N + z;
                 const T c = chi[po];
@@ -662,7 +665,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         __syncthreads();
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (!PM && threadIdx.x < 6) {
         Acc a = {0, 0};
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
             a.add(wacc[w][2 * threadIdx.x]);
@@ -1106,7 +1109,9 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 // kept kx, 1/n^3, Leray projection and the integrating-factor AB2 (Euler on
 // the first step) update of U and H. MODE 1 instead sets U to the projected
 // field (mean kept) and clears H; MODE 2 writes the truncated transform
-// times 1/n^3 to U (no projection; H unused). Each field is transformed in
+// times 1/n^3 to U (no projection; H unused); MODE 3 writes the total
+// pressure coefficients Pi_hat = -i (k . N_hat) / |k|^2 (one field) to U,
+// the gradient part the projection removes. Each field is transformed in
 // place in its staging buffer; kept outputs go to three result tiles.
 // tm: A as rows of 2 Kzp reals, row (f K + ky) n + x.
 template <typename T, int N, int MODE>
@@ -1257,6 +1262,18 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
                 }
                 continue;
             }
+            if constexpr (MODE == 3) {   // Pi_hat = -i (k . N_hat) / |k|^2, Pi_hat(0) = 0
+                const int mx = cmode_of(cx, mmax, K);
+                const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+                const T k2 = kx * kx + ky * ky + kz * kz;
+                const C2 n0 = Rt[idx], n1 = Rt[K * CT + idx], n2 = Rt[2 * K * CT + idx];
+                const T dr = (kx * n0.x + ky * n1.x + kz * n2.x) * invn3;
+                const T di = (kx * n0.y + ky * n1.y + kz * n2.y) * invn3;
+                const bool zero = (mx == 0 && cy == 0 && czz == 0);
+                const T ik2 = zero ? (T)0 : (T)1 / k2;
+                U[o] = cmk<C2>(di * ik2, -dr * ik2);
+                continue;
+            }
             C2 nn[3];
             proj(idx, cx, czz, nn);
             if constexpr (MODE == 1) {
@@ -1338,7 +1355,8 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
 }
 
 // Inverse: B fields 0..2 (z spectral, kz < Kz) -> physical u (3 x n^3 real).
-template <typename T, int N>
+// MODE 1: one field, B field 0 -> u[0..n^3) as u := (inverse) - u.
+template <typename T, int N, int MODE = 0>
 __global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
 k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
     using C2 = cplx<T>;
@@ -1374,6 +1392,16 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
         }
         return cmk<C2>((T)0, (T)0);
     };
+    if constexpr (MODE == 1) {
+        const C2* f0 = B + lo;
+        auto load = [&](int q) -> C2 { return two(f0, f0 + Kzp, q); };
+        auto store = [&](int z, C2 v) {
+            u[po + z] = v.x - u[po + z];
+            u[po + N + z] = v.y - u[po + N + z];
+        };
+        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, (line & 1) == 0);
+        return;
+    }
     {
         auto load = [&](int q) -> C2 { return two(B + lo, B + BS + lo, q); };
         auto store = [&](int z, C2 v) { u[po + z] = v.x; u[N3 + po + z] = v.y; };

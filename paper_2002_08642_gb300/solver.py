@@ -109,6 +109,27 @@ class Solver:
     def forces(self):
         return B.ps_forces(self.ctx)
 
+    def pressure(self, out=None):
+        """Static pressure p = Pi - (1/2)|u|^2 of the current state and mask."""
+        n = self.n
+        if out is None:
+            out = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
+        B.ps_pressure(self.ctx, self._field(out, 1, "out"))
+        return out
+
+    def pressure_loads(self, p, xw, tri, frame):
+        """(p at the nodes, node forces (global frame)) from the pressure p."""
+        for t, nm, dt in ((xw, "xw", torch.float64), (tri, "tri", torch.int32)):
+            if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous %s tensor on %s" % (nm, dt, self.device))
+            if t.dim() != 2 or t.shape[1] != 3:
+                raise ValueError("%s must have shape (k, 3)" % nm)
+        pn = torch.empty(xw.shape[0], dtype=torch.float64, device=self.device)
+        fn = torch.empty((xw.shape[0], 3), dtype=torch.float64, device=self.device)
+        B.ps_pressure_loads(self.ctx, self._field(p, 1, "p"), xw.data_ptr(), xw.shape[0], tri.data_ptr(),
+                            tri.shape[0], B.make_frame(frame), pn.data_ptr(), fn.data_ptr())
+        return pn, fn
+
     def diagnostics(self):
         return B.ps_diagnostics(self.ctx)
 
