@@ -725,7 +725,7 @@ ps_status ps_pressure_loads(ps_ctx* c, const void* p_dev, const double* xw, int3
     const int nb = (n_nodes + 127) / 128;
     if (c->fp64) k_node_pressure<double><<<nb, 128, 0, c->stream>>>(a, (const double*)p_dev, p_nodes_dev);
     else k_node_pressure<float><<<nb, 128, 0, c->stream>>>(a, (const float*)p_dev, p_nodes_dev);
-    k_node_loads<<<nb, 128, 0, c->stream>>>(a, p_nodes_dev, f_nodes_dev);
+    k_node_loads<<<(n_nodes + 3) / 4, 128, 0, c->stream>>>(a, p_nodes_dev, f_nodes_dev);   // a warp per node
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "ps_pressure_loads");
     return PS_OK;

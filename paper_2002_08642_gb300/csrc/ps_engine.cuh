@@ -327,7 +327,7 @@ template <typename T, int N> struct Engine {
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
         k_yinv<T, N, 1><<<grid_ys(k1), thr_s, sm_strided, s>>>(k1, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, N, 1><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)p, tw);
+        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)p, tw);
         return cudaGetLastError();
     }
 

@@ -1355,7 +1355,8 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
 }
 
 // Inverse: B fields 0..2 (z spectral, kz < Kz) -> physical u (3 x n^3 real).
-// MODE 1: one field, B field 0 -> u[0..n^3) as u := (inverse) - u.
+// MODE 1: one field, B field 0 -> u[0..n^3) as u := (inverse) - u, each
+// thread group on a pair of lines (launch (zblocks() + 1) / 2 blocks).
 template <typename T, int N, int MODE = 0>
 __global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
 k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
@@ -1393,13 +1394,17 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
         return cmk<C2>((T)0, (T)0);
     };
     if constexpr (MODE == 1) {
-        const C2* f0 = B + lo;
+        // one field: thread group `line` takes the line pair (2 lid, 2 lid + 1)
+        // (launched with half the blocks, rounded up)
+        const bool on = 2 * lid < (long)N * N;
+        const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
+        const C2* f0 = B + lo2;
         auto load = [&](int q) -> C2 { return two(f0, f0 + Kzp, q); };
         auto store = [&](int z, C2 v) {
-            u[po + z] = v.x - u[po + z];
-            u[po + N + z] = v.y - u[po + N + z];
+            u[po2 + z] = v.x - u[po2 + z];
+            u[po2 + N + z] = v.y - u[po2 + N + z];
         };
-        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, (line & 1) == 0);
+        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, on);
         return;
     }
     {

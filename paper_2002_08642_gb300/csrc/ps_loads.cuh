@@ -68,13 +68,15 @@ __global__ void k_node_pressure(LoadArgs a, const T* __restrict__ pf, double* __
     pn[v] = acc;
 }
 
-// One thread per node: F_v = -p_v sum over the triangles containing v of
-// ((b - a) x (c - a)) / 6 (global frame); triangles in index order.
+// One warp per node: F_v = -p_v sum over the triangles containing v of
+// ((b - a) x (c - a)) / 6 (global frame); the lanes scan the triangles in
+// strided index order and combine by a fixed shuffle tree (deterministic).
 __global__ void k_node_loads(LoadArgs a, const double* __restrict__ pn, double* __restrict__ F) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.n_nodes) return;
+    const int v = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (v >= a.n_nodes) return;   // whole warps leave together
     double s[3] = {0.0, 0.0, 0.0};
-    for (int t = 0; t < a.n_tri; ++t) {
+    for (int t = lane; t < a.n_tri; t += 32) {
         const int i0 = a.tri[3 * t], i1 = a.tri[3 * t + 1], i2 = a.tri[3 * t + 2];
         if (i0 != v && i1 != v && i2 != v) continue;
         double A[3], B[3], C[3];
@@ -87,8 +89,12 @@ __global__ void k_node_loads(LoadArgs a, const double* __restrict__ pn, double* 
         s[1] += e1[2] * e2[0] - e1[0] * e2[2];
         s[2] += e1[0] * e2[1] - e1[1] * e2[0];
     }
-    const double f = -pn[v] / 6.0;
-    for (int r = 0; r < 3; ++r) F[3 * v + r] = f * s[r];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int r = 0; r < 3; ++r) s[r] += __shfl_down_sync(0xffffffffu, s[r], o);
+    if (lane == 0) {
+        const double f = -pn[v] / 6.0;
+        for (int r = 0; r < 3; ++r) F[3 * v + r] = f * s[r];
+    }
 }
 
 }  // namespace ps

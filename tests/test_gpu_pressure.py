@@ -37,8 +37,8 @@ def _case(n, nodes=300):
     return p, u, chi, us, xw, tri, fr
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
-@pytest.mark.parametrize("n", [32, 48])
+@pytest.mark.parametrize("n,prec,tol", [(32, "fp64", 1e-11), (32, "fp32", 2e-5), (48, "fp64", 1e-11),
+                                        (48, "fp32", 2e-5), (12, "fp64", 1e-11), (24, "fp32", 2e-5)])
 def test_pressure_matches_oracle(n, prec, tol):
     p, u, chi, us, xw, tri, fr = _case(n)
     dtype = torch.float64 if prec == "fp64" else torch.float32
