@@ -25,6 +25,12 @@ Readings of points the paper leaves open (each is listed in the design doc):
 * Mean mode k = 0: MEAN_FIXED (default) sets N_hat(0) = 0, so the mean
   velocity stays at its initial value; MEAN_FREE keeps N_hat(0).
 * C_eta of the paper is ``eta`` here.
+* Sponge term (optional, off unless ``set_sponge``): the paper writes it as
+  -(1/C_sp) curl (chi_sp omega) / lap and calls it a vorticity damping term;
+  read literally that sign amplifies (for chi_sp = 1 it is +u/C_sp), so the
+  damping reading is taken: -(1/C_sp) curl^{-1}(chi_sp omega), spectrally
+      S_hat = -(1/C_sp) i k x s_hat / |k|^2,  s_hat = F[chi_sp omega] (2/3 rule),
+  which is -u/C_sp for chi_sp = 1 (solenoidal, so the projection keeps it).
 * Force on the solid from the penalization term, fluid density 1:
       F = (dx^3 / eta) sum_j chi_j (u_j - u_s,j)
       M = (dx^3 / eta) sum_j (x_j - x0) x chi_j (u_j - u_s,j)
@@ -105,6 +111,18 @@ def project(p, Nh):
     return out
 
 
+def sponge_hat(p, sh, c_sp):
+    """-(1/C_sp) i k x s_hat / |k|^2 (zero at k = 0)."""
+    kx, ky, kz = wavevectors(p)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2_safe = np.where(k2 == 0.0, 1.0, k2)
+    sx, sy, sz = sh
+    out = np.stack([1j * (ky * sz - kz * sy), 1j * (kz * sx - kx * sz), 1j * (kx * sy - ky * sx)])
+    out = -out / (c_sp * k2_safe)
+    out[:, 0, 0, 0] = 0.0
+    return out
+
+
 def integrating_factor(p):
     """E = exp(-nu |k|^2 dt) on the half spectrum."""
     kx, ky, kz = wavevectors(p)
@@ -167,6 +185,8 @@ class Solver:
         self.us = np.zeros((3, n, n, n))
         self.F = np.zeros(3)
         self.M = np.zeros(3)
+        self.chi_sp = None
+        self.c_sp = 0.0
 
     def set_velocity(self, u):
         """Transform, truncate and project u; the mean is kept; AB2 restarts."""
@@ -188,6 +208,11 @@ class Solver:
         self.chi = np.asarray(chi, dtype=np.float64)
         self.us = np.asarray(us, dtype=np.float64)
 
+    def set_sponge(self, chi_sp, c_sp):
+        """Sponge mask (n^3) and constant C_sp; chi_sp None turns it off."""
+        self.chi_sp = None if chi_sp is None else np.asarray(chi_sp, dtype=np.float64)
+        self.c_sp = float(c_sp)
+
     def velocity(self):
         return to_physical(self.uh, self.p.n)
 
@@ -200,6 +225,8 @@ class Solver:
         self.F, self.M = penalization_force(p, u, self.chi, self.us)
         nl = nonlinear_physical(u, w, self.chi, self.us, p.eta)
         Nh = to_spectral(nl) * self.keep
+        if self.chi_sp is not None:
+            Nh = Nh + sponge_hat(p, to_spectral(self.chi_sp[None] * w) * self.keep, self.c_sp)
         return project(p, Nh)
 
     def step(self, nsteps=1):
