@@ -148,6 +148,21 @@ ps_status ps_step(ps_ctx* ctx, int32_t nsteps);
  * Host outputs; synchronises the stream. */
 ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
 
+/* Sponge term (Sec. 4.1, Eq. penalized Navier--Stokes: the vorticity
+ * damping term), added to the nonlinear term of every following step:
+ *   S = -(1/C_sp) curl^{-1}(chi_sp omega),  S_hat = -(1/C_sp) i k x s_hat / |k|^2,
+ * s_hat the 2/3-truncated transform of chi_sp omega. (The paper prints the
+ * term with 1/lap and a minus sign, which read literally amplifies; the
+ * damping form its text describes is taken: for chi_sp = 1, S = -u/C_sp.)
+ *   chi_sp_dev  n^3 array [x][y][z] in the context precision, caller-owned;
+ *               read by every step while set, so it must stay valid and
+ *               unchanged until the sponge is turned off. NULL turns it off.
+ *   c_sp        C_sp > 0 (ignored when turning off).
+ * With the sponge on, a step also transforms the three components of
+ * chi_sp omega forward (the z pass's otherwise idle thread groups) and reads
+ * six fields in the x-forward pass. PS_EINVAL for c_sp <= 0. */
+ps_status ps_set_sponge(ps_ctx* ctx, const void* chi_sp_dev, double c_sp);
+
 /* Static pressure p = Pi - (1/2)|u|^2 of the current state with the current
  * mask (Sec. 4.1: Pi = p + (1/2) u.u is the total pressure of the rotational
  * form; the fluid-solid coupling computes p^{n+1} from u^{n+1}). Pi is the

@@ -54,6 +54,7 @@ _SIGS = {
     "ps_forces": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_diagnostics": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_pressure": (c_int32, [c_void_p, c_void_p]),
+    "ps_set_sponge": (c_int32, [c_void_p, c_void_p, c_double]),
     "ps_pressure_loads": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, _P(PsFrame),
                                     c_void_p, c_void_p]),
     "ps_state_size": (c_int32, [c_void_p, _P(c_size_t)]),
@@ -167,6 +168,10 @@ def ps_forces(ctx):
     M = (c_double * 3)()
     check(lib().ps_forces(ctx, F, M), ctx)
     return list(F), list(M)
+
+
+def ps_set_sponge(ctx, chi_sp_ptr, c_sp):
+    check(lib().ps_set_sponge(ctx, c_void_p(chi_sp_ptr) if chi_sp_ptr else None, float(c_sp)), ctx)
 
 
 def ps_pressure(ctx, p_ptr):

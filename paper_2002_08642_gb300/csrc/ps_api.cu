@@ -546,6 +546,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         c->b.tmHp = &c->tmHp;
         c->b.tmBo = &c->tmBo;
         c->b.tmG = nullptr;
+        c->b.chi_sp = nullptr;
         if (p->with_adjoint) {
             if (!encode_rows(&c->tmG, c->adj_spec[2], c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2)) {
                 delete c;
@@ -692,6 +693,18 @@ ps_status ps_step(ps_ctx* c, int32_t nsteps) {
         if (e != cudaSuccess) return cuda_fail(c, e, "ps_step");
         c->nstep++;
     }
+    return PS_OK;
+}
+
+ps_status ps_set_sponge(ps_ctx* c, const void* chi_sp_dev, double c_sp) {
+    if (!c) return PS_EINVAL;
+    if (!chi_sp_dev) {
+        c->b.chi_sp = nullptr;
+        return PS_OK;
+    }
+    if (!(c_sp > 0.0)) return fail(c, PS_EINVAL, "ps_set_sponge: C_sp must be > 0");
+    c->b.chi_sp = chi_sp_dev;
+    c->kp.inv_csp = 1.0 / c_sp;
     return PS_OK;
 }
 

@@ -43,6 +43,7 @@ struct Bufs {
     const CUtensorMap* tmHp;
     const CUtensorMap* tmBo; // B, y-forward box of the slab pipeline
     const CUtensorMap* tmG;  // adjoint G as rows of 2 Kzp reals, x-inverse box (null without adjoint)
+    const void* chi_sp;      // sponge mask (n^3, caller-owned), null when the sponge term is off
     cudaStream_t aux[2];     // slab pipeline streams
     cudaEvent_t sev[3];      // fork/join events of the slab pipeline
 };
@@ -115,6 +116,11 @@ template <typename T, int N> struct Engine {
     }
     static constexpr size_t sm_x1 = (size_t)GE::y2_smem(GE::CX1);
     static constexpr size_t sm_x5t = (size_t)GE::x5_smem(GE::CX5);
+    static constexpr size_t sm_x5s = sm_x5t;   // the sponge variant keeps three result tiles
+    static int& x5sgrid() {
+        static int g = 0;
+        return g;
+    }
     static constexpr int thr_x1 = GE::CX1 * GE::G;
     static constexpr int thr_x5 = GE::CX5 * GE::G;
     static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2, GE::Y2NB);
@@ -178,6 +184,12 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 3>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 0, true>, sm_x5s))) return e;
+        if ((e = attr(k_zpass<T, N, false, true>, sm_zp))) return e;
+        if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 6>, sm_y4))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, true>, thr_x5, sm_x5s)))
+            return e;
+        x5sgrid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N>, thr_x1, sm_x1))) return e;
         x1grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
@@ -210,7 +222,26 @@ template <typename T, int N> struct Engine {
         k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
 #endif
         if (ev) cudaEventRecord(ev[1], s);
-        const int S = nslab();
+        const int S = b.chi_sp ? 1 : nslab();   // the sponge variant runs the plain serial passes
+        if (b.chi_sp) {
+            KP k1 = kp;
+            k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+            if (ev) cudaEventRecord(ev[2], s);
+            k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+            if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
+            k_zpass<T, N, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+                                                                     b.flag, b.partial, tw, b.err, nullptr,
+                                                                     (const T*)b.chi_sp);
+            if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
+            k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+            if (ev) cudaEventRecord(ev[7], s);
+            if (ev) cudaEventRecord(ev[2 + 6 * kMaxSlabs], s);
+            k_xfwd_tma<T, N, 0, true><<<x5sgrid(), thr_x5, sm_x5s, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
+                                                                       (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez,
+                                                                       first, tw, b.err);
+            if (ev) cudaEventRecord(ev[3 + 6 * kMaxSlabs], s);
+            return cudaGetLastError();
+        }
         if (S <= 1) {
             KP k1 = kp;
             k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
@@ -218,7 +249,7 @@ template <typename T, int N> struct Engine {
             k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
             if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
             k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                        b.flag, b.partial, tw, b.err, nullptr);
+                                                        b.flag, b.partial, tw, b.err, nullptr, nullptr);
             if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
             k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
             if (ev) cudaEventRecord(ev[7], s);
@@ -238,7 +269,7 @@ template <typename T, int N> struct Engine {
                 k_yinv_tma<T, N><<<ovl_y2(), thr_y2, sm_y2, st>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
                 if (e) { cudaEventRecord(e[1], st); cudaEventRecord(e[2], st); }
                 k_zpass<T, N><<<ovl_z(), thr_zp, sm_zp, st>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                             b.flag, b.partial, tw, b.err, nullptr);
+                                                             b.flag, b.partial, tw, b.err, nullptr, nullptr);
                 if (e) { cudaEventRecord(e[3], st); cudaEventRecord(e[4], st); }
                 k_yfwd_tma<T, N, GE::CY4O><<<ovl_y4(), thr_y4o, sm_y4o, st>>>(*b.tmBo, k1, (C2*)b.A, tw, b.err);
                 if (e) cudaEventRecord(e[5], st);
@@ -320,7 +351,7 @@ template <typename T, int N> struct Engine {
         k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         k_zpass<T, N, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
-                                                          b.partial, tw, b.err, (T*)p);
+                                                          b.partial, tw, b.err, (T*)p, nullptr);
         k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
         C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * GE::KZP;
         k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,

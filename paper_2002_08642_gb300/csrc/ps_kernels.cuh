@@ -104,6 +104,7 @@ struct KP {
     int mean_free;
     int xs0, xsn;     // x planes [xs0, xs0 + xsn) handled by the y and z passes
     int part_off;     // first force-partial slot of this z-pass launch
+    double inv_csp;   // 1 / C_sp of the sponge term (used by the sponge variants only)
 };
 
 __device__ __forceinline__ int mode_of(int q, int n) { return q < n / 2 ? q : q - n; }
@@ -205,8 +206,8 @@ template <typename T, int N> struct Geo {
     static constexpr int y4_smem(int c) {   // y forward: 2 staging tiles of N rows, transformed in place
         return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c)) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
-    static constexpr int x5_smem(int c) {   // x forward: 2 staging tiles (N rows) + 3 kept-mode result tiles
-        return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c) + 3 * K) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
+    static constexpr int x5_smem(int c, int nf = 3) {   // x forward: 2 staging tiles (N rows) + nf result tiles
+        return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c) + nf * K) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
     // widest tile (at most cmax complex, at least 2) whose shared memory fits
     static constexpr int pick_c(int which, int kb, int cmax) {
@@ -421,11 +422,15 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // writes in place and no reordering pass is needed.
 // PM (pressure evaluation): also writes (1/2)|u|^2 to half_u2 (n^3,
 // [x][y][z]) and leaves the force partials of the last step untouched.
-template <typename T, int N, bool PM = false>
+// SP (sponge term on): also s = chi_sp omega, transformed forward like n
+// (s_x + i s_y per line by the third thread group, s_z of line pairs by the
+// odd lines' second group, the groups that are otherwise idle) into B
+// fields 3..5.
+template <typename T, int N, bool PM = false, bool SP = false>
 __global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
         const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
-        int* __restrict__ err, T* __restrict__ half_u2) {
+        int* __restrict__ err, T* __restrict__ half_u2, const T* __restrict__ chi_sp) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
@@ -594,6 +599,16 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             T nx0, ny0, nz0, nx1, ny1, nz1;
             nonlinear(l, z, a, nx0, ny0, nz0);
             nonlinear(l + 1, z, a, nx1, ny1, nz1);
+            if constexpr (SP) {
+                // s = chi_sp omega of both lines, read before their slots are reused
+                const long lid0 = (long)b * LZ + l;
+                const T c0 = chi_sp[(size_t)lid0 * N + z], c1 = chi_sp[(size_t)(lid0 + 1) * N + z];
+                const T wx0 = tile(l, 1)[a].y, wx1 = tile(l + 1, 1)[a].y;
+                const C2 w0 = tile(l, 2)[a], w1 = tile(l + 1, 2)[a];
+                tile(l, 2)[a] = cmk<C2>(c0 * wx0, c0 * w0.x);
+                tile(l + 1, 2)[a] = cmk<C2>(c1 * wx1, c1 * w1.x);
+                tile(l + 1, 1)[a] = cmk<C2>(c0 * w0.y, c1 * w1.y);
+            }
             tile(l, 0)[a] = cmk<C2>(nx0, ny0);
             tile(l + 1, 0)[a] = cmk<C2>(nx1, ny1);
             tile(l, 1)[a] = cmk<C2>(nz0, nz1);
@@ -615,8 +630,9 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         __syncthreads();
         {
             // forward lines: (l, 0) for every l, (l, 1) for even l; others idle
-            const bool active = (pr == 0) || (pr == 1 && (pl & 1) == 0);
-            const int tbase = (int)(tile(pl, pr == 2 ? 1 : pr) - tiles);
+            // (with the sponge: every tile)
+            const bool active = SP || (pr == 0) || (pr == 1 && (pl & 1) == 0);
+            const int tbase = (int)(tile(pl, SP ? pr : (pr == 2 ? 1 : pr)) - tiles);
             auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
             if constexpr (Z3) {
                 const int sub = g / GM, gm = g % GM;
@@ -633,9 +649,10 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         if constexpr (Z3) {
             // radix-3 recombination of the three sub-line spectra, kept modes only
             const T h3 = (T)0.86602540378443864676;
-            for (int idx = threadIdx.x; idx < (LZ + LZ / 2) * M; idx += blockDim.x) {
+            constexpr int NREC = SP ? 3 * LZ : LZ + LZ / 2;   // transformed tiles
+            for (int idx = threadIdx.x; idx < NREC * M; idx += blockDim.x) {
                 const int fl2 = idx / M, kq = idx % M;
-                C2* t = fl2 < LZ ? tile(fl2, 0) : tile(2 * (fl2 - LZ), 1);
+                C2* t = SP ? tile(fl2 % LZ, fl2 / LZ) : (fl2 < LZ ? tile(fl2, 0) : tile(2 * (fl2 - LZ), 1));
                 const C2 F0 = t[zad(kq)], F1 = t[zad(M + kq)], F2 = t[zad(2 * M + kq)];
                 const C2 G1 = cmul(F1, cconj(tw3[kq])), G2 = cmul(F2, cconj(tw3[M + kq]));
                 const C2 Zk = cadd(F0, cadd(G1, G2));
@@ -661,6 +678,16 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             const C2 wk = t1[zad(k)], wm = t1[zad(m)];
             B[2 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
                                          : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
+            if constexpr (SP) {
+                const C2* t2 = tile(l, 2);
+                const C2* t3 = tile(l | 1, 1);
+                const C2 sk = t2[zad(k)], sm = t2[zad(m)];
+                B[3 * BS + lo + k] = cmk<C2>((T)0.5 * (sk.x + sm.x), (T)0.5 * (sk.y - sm.y));
+                B[4 * BS + lo + k] = cmk<C2>((T)0.5 * (sk.y + sm.y), (T)0.5 * (sm.x - sk.x));
+                const C2 qk = t3[zad(k)], qm = t3[zad(m)];
+                B[5 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (qk.y + qm.y), (T)0.5 * (qm.x - qk.x))
+                                             : cmk<C2>((T)0.5 * (qk.x + qm.x), (T)0.5 * (qk.y - qm.y));
+            }
         }
         __syncthreads();
     }
@@ -893,7 +920,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 
 // pass 4: y-forward of the three fields, B (all y rows) -> A (kept ky rows).
 // tm: B as a 2-D array of 6 n n rows of 2 Kzp reals.
-template <typename T, int N, int CTV>
+template <typename T, int N, int CTV, int NF = 3>
 __global__ void __launch_bounds__(CTV * Geo<T, N>::G)
 k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -903,7 +930,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "y-forward staging must be contiguous in y");
     constexpr int NTZ = KZP / CT;
-    const int NITEM = kp.xsn * NTZ * 3;   // items of this launch's x planes
+    const int NITEM = kp.xsn * NTZ * NF;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -925,7 +952,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     const C2* tw3 = load_tw_split<T, N>(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int i, int buf) {  // one thread
-        const int f = i % 3, t = i / 3, x = kp.xs0 + t / NTZ, czt = t % NTZ;
+        const int f = i % NF, t = i / NF, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -945,7 +972,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
             }
             break;
         }
-        const int f = i % 3, t = i / 3, x = kp.xs0 + t / NTZ, czt = t % NTZ;
+        const int f = i % NF, t = i / NF, x = kp.xs0 + t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         C2* Sb = S + (size_t)buf * RS * CT;
@@ -1114,7 +1141,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 // the gradient part the projection removes. Each field is transformed in
 // place in its staging buffer; kept outputs go to three result tiles.
 // tm: A as rows of 2 Kzp reals, row (f K + ky) n + x.
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, bool SP = false>
 __global__ void __launch_bounds__(Geo<T, N>::CX5 * Geo<T, N>::G)
 k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmu,
            const __grid_constant__ CUtensorMap tmh, KP kp, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H,
@@ -1134,6 +1161,10 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
         if (threadIdx.x == 0) atomicExch(err, 2);
         return;
     }
+    // fields read: n (A fields 0..2), with the sponge first s (A fields 3..5),
+    // whose sponge term -(1/C_sp) i k x s_hat/|k|^2 the n transforms add onto
+    constexpr int NF = SP ? 6 : 3;
+    auto field = [](int j) { return SP ? (j < 3 ? j + 3 : j - 3) : j; };
     C2* Rt = S + 2 * RS * CT;                             // [3][K][CT]
     C2* tw = Rt + 3 * K * CT;
     __shared__ __align__(8) uint64_t bar[2];
@@ -1149,7 +1180,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
     const C2* tw3 = load_tw_split<T, N>(tw, twg, GE::tw_n);
     __syncthreads();
     auto issue = [&](int L) {  // one thread
-        const int t = blockIdx.x + (L / 3) * gridDim.x, f = L % 3, buf = L & 1;
+        const int t = blockIdx.x + (L / NF) * gridDim.x, f = field(L % NF), buf = L & 1;
         if (t >= NTILE) return;
         const int cy = t / NTZ, czt = t % NTZ;
         fence_proxy_async();
@@ -1174,8 +1205,9 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             tma_prefetch_2d(first ? &tmu : &tmh, 2 * czt * CT, (f * K + cy) * K + b * BRK);
         }
 #pragma unroll 1
-        for (int f = 0; f < 3; ++f) {
-            const int L = 3 * ti + f, buf = L & 1;
+        for (int j = 0; j < NF; ++j) {
+            const int L = NF * ti + j, buf = L & 1, f = field(j) % 3;
+            const bool acc = SP && j >= 3;   // n onto the sponge term
             if (threadIdx.x == 0) issue(L + 1);
             const bool ok = mbar_wait(&bar[buf], (uint32_t)((L >> 1) & 1));
             if (__syncthreads_or(!ok)) {
@@ -1203,18 +1235,47 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
                     C2 Zk, Zm;
                     split3_out(Sb[(3 * kq) * CT + c], Sb[(3 * kq + 1) * CT + c], Sb[(3 * kq + 2) * CT + c], tw3, kq,
                                M, Zk, Zm);
-                    Rf[kq * CT + c] = Zk;                                 // mode kq
-                    if (kq > 0) Rf[(kq + M - 1) * CT + c] = Zm;           // mode kq - M
+                    C2& r0 = Rf[kq * CT + c];                             // mode kq
+                    r0 = acc ? cadd(r0, Zk) : Zk;
+                    if (kq > 0) {                                          // mode kq - M
+                        C2& r1 = Rf[(kq + M - 1) * CT + c];
+                        r1 = acc ? cadd(r1, Zm) : Zm;
+                    }
                 }
             } else {
                 auto addr = [&](int p) { return (int)(Sb - S) + p * CT + col; };
                 auto store = [&](int q, C2 v) {
                     const int m = mode_of(q, N);
-                    if (m <= mmax && m >= -mmax) Rf[cidx_of(m, K) * CT + col] = v;
+                    if (m <= mmax && m >= -mmax) {
+                        C2& r = Rf[cidx_of(m, K) * CT + col];
+                        r = acc ? cadd(r, v) : v;
+                    }
                 };
                 LineFFT<T, N, -1>::template run<true>(S, tw, addr, g, noload, store);
             }
             __syncthreads();
+            if constexpr (SP) {
+                if (j == 2) {   // s_hat complete: replace it by the sponge term
+                    const T myy = (T)cmode_of(cy, mmax, K);
+                    for (int idx = threadIdx.x; idx < K * CT; idx += blockDim.x) {
+                        const int cx = idx / CT, czz = czt * CT + idx % CT;
+                        const int mx = cmode_of(cx, mmax, K);
+                        const T kx = s * (T)mx, ky = s * myy, kz = s * (T)czz;
+                        const T k2 = kx * kx + ky * ky + kz * kz;
+                        const C2 s0 = Rt[idx], s1 = Rt[K * CT + idx], s2 = Rt[2 * K * CT + idx];
+                        const bool zero = (mx == 0 && cy == 0 && czz == 0);
+                        const T fsp = zero ? (T)0 : -(T)kp.inv_csp / k2;
+                        // i (k x s): (re, im) -> (-im, re)
+                        const T ax = ky * s2.x - kz * s1.x, bx = ky * s2.y - kz * s1.y;
+                        const T ay = kz * s0.x - kx * s2.x, by = kz * s0.y - kx * s2.y;
+                        const T az = kx * s1.x - ky * s0.x, bz = kx * s1.y - ky * s0.y;
+                        Rt[idx] = cmk<C2>(-fsp * bx, fsp * ax);
+                        Rt[K * CT + idx] = cmk<C2>(-fsp * by, fsp * ay);
+                        Rt[2 * K * CT + idx] = cmk<C2>(-fsp * bz, fsp * az);
+                    }
+                    __syncthreads();
+                }
+            }
         }
         if (stop) break;
         const T my = (T)cmode_of(cy, mmax, K);

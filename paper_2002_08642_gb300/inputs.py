@@ -137,10 +137,22 @@ def flapping_amplitudes(xw, seed=42, amp=0.05):
     return amp * s * s * (0.9 + 0.1 * zeta)
 
 
-def revolving_wing(t, xw0, a, centre=(2.0, 2.0, 2.0), omega=1.0, pitch_deg=45.0):
-    """Node positions/velocities in the wing frame and the frame at time t."""
+def revolving_angle(t, omega=1.0, tau=None):
+    """Rotation angle and rate of the revolving wing. tau None: constant rate
+    omega. Otherwise the startup of Sec. 4.2 (rigid revolving wing),
+    phi(t) = omega (tau e^{-t/tau} + t - tau), rate omega (1 - e^{-t/tau})."""
+    if tau is None:
+        return omega * t, omega
+    e = math.exp(-t / tau)
+    return omega * (tau * e + t - tau), omega * (1.0 - e)
+
+
+def revolving_wing(t, xw0, a, centre=(2.0, 2.0, 2.0), omega=1.0, pitch_deg=45.0, tau=None):
+    """Node positions/velocities in the wing frame and the frame at time t
+    (tau: optional startup time of the rotation, see ``revolving_angle``)."""
     normal = np.array([0.0, 0.0, 1.0])
     xw = xw0 + (a * math.sin(2.0 * math.pi * t))[:, None] * normal[None]
     vw = (a * 2.0 * math.pi * math.cos(2.0 * math.pi * t))[:, None] * normal[None]
-    R = rot_z(omega * t) @ rot_y(pitch_deg)
-    return xw, vw, frame(R, centre, (0.0, 0.0, 0.0), (0.0, 0.0, omega))
+    phi, rate = revolving_angle(t, omega, tau)
+    R = rot_z(phi) @ rot_y(pitch_deg)
+    return xw, vw, frame(R, centre, (0.0, 0.0, 0.0), (0.0, 0.0, rate))

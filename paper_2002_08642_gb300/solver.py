@@ -109,6 +109,16 @@ class Solver:
     def forces(self):
         return B.ps_forces(self.ctx)
 
+    def set_sponge(self, chi_sp, c_sp=1.0):
+        """Turn the sponge term on with mask chi_sp (kept referenced: the
+        library reads it every step) or off with None."""
+        if chi_sp is None:
+            B.ps_set_sponge(self.ctx, 0, 0.0)
+            self._sponge = None
+            return
+        B.ps_set_sponge(self.ctx, self._field(chi_sp, 1, "chi_sp"), c_sp)
+        self._sponge = chi_sp
+
     def pressure(self, out=None):
         """Static pressure p = Pi - (1/2)|u|^2 of the current state and mask."""
         n = self.n

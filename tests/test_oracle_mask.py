@@ -115,3 +115,19 @@ def test_tanh_profile_dense():
     assert np.all(arg >= 0)
     assert np.allclose(chi, 0.5 * (1 - np.tanh((best - 2 * dx) / (1.5 * dx))), atol=0)
     assert abs(OM.chi_tanh(2 * dx, 2 * dx, 1.5 * dx) - 0.5) < 1e-16
+
+
+def test_revolving_startup_angle_and_rate():
+    """phi(t) = tau e^{-t/tau} + t - tau: phi(0) = 0, phi'(0) = 0, the rate is
+    its derivative, and for t >> tau the angle trails the constant-rate one
+    by tau."""
+    from paper_2002_08642_gb300 import inputs
+    tau = 0.4
+    assert inputs.revolving_angle(0.0, 1.0, tau) == (0.0, 0.0)
+    for t in (0.1, 0.5, 2.0):
+        h = 1e-6
+        d = (inputs.revolving_angle(t + h, 1.0, tau)[0] - inputs.revolving_angle(t - h, 1.0, tau)[0]) / (2 * h)
+        assert abs(d - inputs.revolving_angle(t, 1.0, tau)[1]) < 1e-8
+    phi, rate = inputs.revolving_angle(20.0, 1.0, tau)
+    assert abs(phi - (20.0 - tau)) < 1e-12 and abs(rate - 1.0) < 1e-12
+    assert inputs.revolving_angle(3.0, 2.0, None) == (6.0, 2.0)
