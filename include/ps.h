@@ -262,6 +262,82 @@ ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision, double L, 
 /* Text of the last error on this context ("" if none). */
 const char* ps_last_error(const ps_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Mass-spring network of the wing (Sec. 2.1-2.2). Host code, host memory,
+ * double precision; no CUDA call. Node arrays are n_nodes x 3, row-major.
+ *
+ * Springs (Eq. extension_spring, Eq. two_bending_angles): an extension
+ * spring (i, j) stores k^e and its rest length |x0_j - x0_i|; a bending
+ * spring (i, j, k) stores k^b and the rest angles theta^y_0, theta^z_0 of
+ * x0, theta^y = atan2[(x_j-x_i)(y_k-y_j) - (x_k-x_j)(y_j-y_i),
+ * (x_j-x_i)(x_k-x_j) + (y_j-y_i)(y_k-y_j)], theta^z the same with z for y.
+ * Internal forces are minus the gradient of
+ *   E = sum (1/2) k^e (l - l_0)^2 + sum (1/2) k^b [(dtheta^y)^2 + (dtheta^z)^2],
+ * angle changes taken in (-pi, pi]. The extension force is the printed
+ * one; the bending force is the gradient of the bending energy (the
+ * printed bending force has no lever length; Eq. EI_k_relation, which sets
+ * k^b = (EI/l_b) n(2n+1)/(2(n+1)), equates energies). Fixed nodes never
+ * move; the others follow m dv/dt = F_int + F_ext (Eq. Newton_law).
+ *
+ * Moving frame: the network may be solved in a frame with origin
+ * acceleration A_O, angular velocity Omega and angular acceleration
+ * dOmega, all expressed in the frame's own axes; each free node then also
+ * feels -m (A_O + dOmega x x + Omega x (Omega x x) + 2 Omega x v).
+ * -------------------------------------------------------------------- */
+typedef struct ps_ms ps_ms;
+
+typedef struct {
+    double A_O[3];
+    double Omega[3];
+    double dOmega[3];
+} ps_ms_frame;
+
+/* Build a network. mass (n_nodes, > 0), x0 (rest and initial positions),
+ * v0 (initial velocities; NULL = 0), fixed (n_nodes flags; NULL = none),
+ * ext_ij (n_ext x 2), ke (n_ext), bend_ijk (n_bend x 3), kb (n_bend).
+ * Inputs are copied. The free nodes are ordered by reverse Cuthill--McKee
+ * for a banded Newton matrix. PS_EINVAL for an out-of-range or repeated
+ * index or a mass <= 0; PS_ENOMEM if allocation fails. */
+ps_status ps_ms_create(int32_t n_nodes, const double* mass, const double* x0, const double* v0,
+                       const unsigned char* fixed, int32_t n_ext, const int32_t* ext_ij, const double* ke,
+                       int32_t n_bend, const int32_t* bend_ijk, const double* kb, ps_ms** out);
+ps_status ps_ms_destroy(ps_ms* m);
+
+/* Free-node count and the node bandwidth of the Newton matrix. */
+ps_status ps_ms_info(const ps_ms* m, int32_t* n_free, int32_t* bandwidth);
+
+/* Internal spring forces at positions x (n_nodes x 3) into f_out. */
+ps_status ps_ms_forces(const ps_ms* m, const double* x, double* f_out);
+
+/* Current positions/velocities (either output may be NULL). */
+ps_status ps_ms_state(const ps_ms* m, double* x_out, double* v_out);
+
+/* Replace positions and velocities (v NULL = 0; fixed nodes get v = 0)
+ * and forget the step history: the next step is backward Euler. */
+ps_status ps_ms_set_state(ps_ms* m, const double* x, const double* v);
+
+/* One time step of length dt (Eq. discretized_ODEs, variable-step BDF2,
+ * xi = dt / previous dt; the first step after create/set_state/equilibrium
+ * is backward Euler). f_ext (n_nodes x 3, NULL = 0) is the external force
+ * held over the step; frame (NULL = inertial) adds the fictitious forces
+ * at the new time level. Newton--Raphson on the positions (velocities
+ * eliminated), starting from the current state, until the L2 norm of the
+ * update is below tol * max(1, |x|). Returns the iterations in *iters_out
+ * (may be NULL). PS_ENUMERIC, state unchanged, if Newton does not converge
+ * in max_iter iterations or its matrix is singular. */
+ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame* frame, double tol,
+                     int32_t max_iter, int32_t* iters_out);
+
+/* Static equilibrium F_int(x) + f_ext = 0 by Newton--Raphson with the load
+ * raised in load_steps equal increments (each converged to tol as in
+ * ps_ms_step). Sets the positions, zero velocities, clears the history.
+ * PS_ENUMERIC (state unchanged) if a load increment does not converge. */
+ps_status ps_ms_equilibrium(ps_ms* m, const double* f_ext, int32_t load_steps, double tol, int32_t max_iter,
+                            int32_t* iters_out);
+
+/* Text of the last error on this network ("" if none). */
+const char* ps_ms_last_error(const ps_ms* m);
+
 #ifdef __cplusplus
 }
 #endif

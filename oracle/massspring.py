@@ -16,12 +16,18 @@ Test infrastructure only (see ``oracle/__init__``).
   forces here are minus the gradient of this energy, which is what the
   k^b - EI relation of Eq. (EI_k_relation) assumes. Here the gradient is
   taken by central differences of the energy.
-* Dynamics m_i dv_i/dt = F_int + F_ext, nodes flagged fixed do not move.
+* Dynamics m_i dv_i/dt = F_int + F_ext (Eq. Newton_law), nodes flagged
+  fixed do not move; in a moving frame each node also feels
+  -m (A_O + dOmega x x + Omega x (Omega x x) + 2 Omega x v).
   Variable-step BDF2 (Eq. discretized_ODEs),
       q^{n+1} - (1+xi)^2/(1+2xi) q^n + xi^2/(1+2xi) q^{n-1} = (1+xi)/(1+2xi) dt f(q^{n+1}),
   xi = dt^n / dt^{n-1}; the first step is backward Euler (xi = 0). Newton on
   the positions (v eliminated), Jacobian by central differences, stopping at
   a relative or absolute L2 change below tol.
+* Parity pinned: the extension force, the small-deflection beam, the
+  static large-deflection table, BDF2 order, the backward-Euler start and
+  the fictitious forces are each checked against a closed form or the
+  paper's printed values in the tests.
 """
 import math
 
@@ -117,9 +123,23 @@ def _fd_jacobian(net, x, free, h=1e-6):
     return J
 
 
-def bdf2_step(net, x, v, xm1, vm1, dt, dt_prev, f_ext, tol=1e-10, max_iter=30):
-    """One variable-step BDF2 step (backward Euler when xm1 is None).
-    Returns (x_new, v_new, iterations)."""
+def fictitious_forces(net, x, v, frame):
+    """Forces of a moving frame on each node: -m (A_O + dOmega x x +
+    Omega x (Omega x x) + 2 Omega x v), frame = dict(A_O, Omega, dOmega) in
+    the frame's own axes (the wing frame of Sec. 4.1, Eq.
+    relative_velocities, is such a frame)."""
+    A = np.asarray(frame.get("A_O", (0.0, 0.0, 0.0)), dtype=np.float64)
+    W = np.asarray(frame.get("Omega", (0.0, 0.0, 0.0)), dtype=np.float64)
+    dW = np.asarray(frame.get("dOmega", (0.0, 0.0, 0.0)), dtype=np.float64)
+    acc = A[None] + np.cross(dW[None], x) + np.cross(W[None], np.cross(W[None], x)) + 2.0 * np.cross(W[None], v)
+    return -net.mass[:, None] * acc
+
+
+def bdf2_step(net, x, v, xm1, vm1, dt, dt_prev, f_ext, tol=1e-10, max_iter=30, frame=None):
+    """One variable-step BDF2 step (backward Euler when xm1 is None), in a
+    moving frame when ``frame`` is given. Newton on the free positions y
+    with v = (y - hx)/(c dt) eliminated; the Jacobian of the whole residual
+    by central differences. Returns (x_new, v_new, iterations)."""
     xi = 0.0 if xm1 is None else dt / dt_prev
     a = (1 + xi) ** 2 / (1 + 2 * xi)
     b = xi * xi / (1 + 2 * xi)
@@ -131,22 +151,33 @@ def bdf2_step(net, x, v, xm1, vm1, dt, dt_prev, f_ext, tol=1e-10, max_iter=30):
     f_ext = np.asarray(f_ext, dtype=np.float64)
     hx = (a * x - b * xm1).ravel()
     hv = (a * v - b * vm1).ravel()
-    y = x.copy()
+
+    def residual(yf):
+        # velocity equation v(y) - hv - c dt f(y)/m on the free coordinates
+        y = yf.reshape(x.shape)
+        vy = (yf - hx) / (c * dt)
+        F = net.forces(y) + f_ext
+        if frame is not None:
+            F = F + fictitious_forces(net, y, vy.reshape(x.shape), frame)
+        return (vy - hv - c * dt * minv * F.ravel())[free]
+
+    yf = x.ravel().copy()
+    idx = np.nonzero(free)[0]
     it = 0
     for it in range(1, max_iter + 1):
-        # v = (y - hx)/(c dt); residual of the velocity equation
-        F = (net.forces(y) + f_ext).ravel()
-        vy = (y.ravel() - hx) / (c * dt)
-        r = (vy - hv - c * dt * minv * F)[free]
-        K = _fd_jacobian(net, y, free)
-        J = np.eye(r.size) / (c * dt) - c * dt * minv[free][:, None] * K
+        r = residual(yf)
+        J = np.zeros((idx.size, idx.size))
+        h = 1e-6 * max(1.0, float(np.max(np.abs(yf))))
+        for col, q in enumerate(idx):
+            yp = yf.copy(); yp[q] += h
+            ym = yf.copy(); ym[q] -= h
+            J[:, col] = (residual(yp) - residual(ym)) / (2 * h)
         dy = np.linalg.solve(J, -r)
-        yf = y.ravel().copy()
         yf[free] += dy
-        y = yf.reshape(x.shape)
         if np.linalg.norm(dy) < tol * max(1.0, np.linalg.norm(yf[free])):
             break
-    vnew = ((y.ravel() - hx) / (c * dt)).reshape(x.shape)
+    y = yf.reshape(x.shape)
+    vnew = ((yf - hx) / (c * dt)).reshape(x.shape)
     vnew[net.fixed] = 0.0
     return y, vnew, it
 

@@ -33,6 +33,10 @@ class PsFrame(ctypes.Structure):
     _fields_ = [("R", c_double * 9), ("X_O", c_double * 3), ("V_O", c_double * 3), ("Omega", c_double * 3)]
 
 
+class PsMsFrame(ctypes.Structure):
+    _fields_ = [("A_O", c_double * 3), ("Omega", c_double * 3), ("dOmega", c_double * 3)]
+
+
 class PsError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
@@ -69,6 +73,16 @@ _SIGS = {
     "ps_last_error": (ctypes.c_char_p, [c_void_p]),
     "ps_penalization_force_noalloc": (c_int32, [c_int32, c_int32, c_double, c_double, _P(c_double), c_void_p,
                                                 c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ps_ms_create": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                               c_int32, c_void_p, c_void_p, _P(c_void_p)]),
+    "ps_ms_destroy": (c_int32, [c_void_p]),
+    "ps_ms_info": (c_int32, [c_void_p, _P(c_int32), _P(c_int32)]),
+    "ps_ms_forces": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ps_ms_state": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ps_ms_set_state": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "ps_ms_step": (c_int32, [c_void_p, c_double, c_void_p, _P(PsMsFrame), c_double, c_int32, _P(c_int32)]),
+    "ps_ms_equilibrium": (c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, _P(c_int32)]),
+    "ps_ms_last_error": (ctypes.c_char_p, [c_void_p]),
 }
 
 _lib = None
@@ -256,4 +270,62 @@ def make_frame(fr):
         f.X_O[i] = float(fr["X_O"][i])
         f.V_O[i] = float(fr.get("V_O", (0, 0, 0))[i])
         f.Omega[i] = float(fr.get("Omega", (0, 0, 0))[i])
+    return f
+
+
+# ------------------------------------------------------------- mass-spring
+def ms_check(status, m):
+    if status != PS_OK:
+        raw = lib().ps_ms_last_error(m) if m else None
+        raise PsError(status, raw.decode() if raw else "")
+
+
+def ps_ms_create(n_nodes, mass_ptr, x0_ptr, v0_ptr, fixed_ptr, n_ext, ext_ptr, ke_ptr, n_bend, bend_ptr, kb_ptr):
+    m = c_void_p(0)
+    check(lib().ps_ms_create(int(n_nodes), c_void_p(mass_ptr), c_void_p(x0_ptr), c_void_p(v0_ptr),
+                             c_void_p(fixed_ptr), int(n_ext), c_void_p(ext_ptr), c_void_p(ke_ptr), int(n_bend),
+                             c_void_p(bend_ptr), c_void_p(kb_ptr), ctypes.byref(m)))
+    return m
+
+
+def ps_ms_destroy(m):
+    check(lib().ps_ms_destroy(m))
+
+
+def ps_ms_info(m):
+    nf, bw = c_int32(0), c_int32(0)
+    ms_check(lib().ps_ms_info(m, ctypes.byref(nf), ctypes.byref(bw)), m)
+    return nf.value, bw.value
+
+
+def ps_ms_forces(m, x_ptr, f_ptr):
+    ms_check(lib().ps_ms_forces(m, c_void_p(x_ptr), c_void_p(f_ptr)), m)
+
+
+def ps_ms_state(m, x_ptr, v_ptr):
+    ms_check(lib().ps_ms_state(m, c_void_p(x_ptr), c_void_p(v_ptr)), m)
+
+
+def ps_ms_set_state(m, x_ptr, v_ptr):
+    ms_check(lib().ps_ms_set_state(m, c_void_p(x_ptr), c_void_p(v_ptr)), m)
+
+
+def ps_ms_step(m, dt, fext_ptr, frame, tol, max_iter):
+    it = c_int32(0)
+    fr = ctypes.byref(frame) if frame is not None else None
+    ms_check(lib().ps_ms_step(m, float(dt), c_void_p(fext_ptr), fr, float(tol), int(max_iter), ctypes.byref(it)), m)
+    return it.value
+
+
+def ps_ms_equilibrium(m, fext_ptr, load_steps, tol, max_iter):
+    it = c_int32(0)
+    ms_check(lib().ps_ms_equilibrium(m, c_void_p(fext_ptr), int(load_steps), float(tol), int(max_iter),
+                                     ctypes.byref(it)), m)
+    return it.value
+
+
+def make_ms_frame(A_O=(0.0, 0.0, 0.0), Omega=(0.0, 0.0, 0.0), dOmega=(0.0, 0.0, 0.0)):
+    f = PsMsFrame()
+    for i in range(3):
+        f.A_O[i], f.Omega[i], f.dOmega[i] = float(A_O[i]), float(Omega[i]), float(dOmega[i])
     return f

@@ -1,0 +1,172 @@
+"""Host mass-spring network through the C ABI (ps_ms_* of libps, Sec.
+2.1-2.4) against the oracle and the paper's printed values. No GPU: the
+network is host code."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import massspring as OM
+from paper_2002_08642_gb300 import binding as B
+from paper_2002_08642_gb300 import build as pbuild
+from paper_2002_08642_gb300.massspring import MassSpring, cantilever
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cantilever_large_deflection.txt")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    pbuild.build()
+
+
+def random_network(seed=5, n=9):
+    """Two bent veins of 3-D points joined by extension springs, first two
+    nodes fixed (bending springs need a nonzero x extent)."""
+    rng = np.random.default_rng(seed)
+    x0 = np.zeros((n, 3))
+    x0[:, 0] = np.arange(n) * 0.1
+    x0[:, 1:] = 0.03 * rng.normal(size=(n, 2))
+    x0[n // 2:, 1] += 0.15
+    ext = [(i, i + 1) for i in range(n - 1)] + [(i, i + n // 2) for i in range(n - n // 2)]
+    bend = [(i, i + 1, i + 2) for i in range(n - 2)]
+    ke = rng.uniform(50.0, 200.0, len(ext))
+    kb = rng.uniform(0.05, 0.2, len(bend))
+    mass = rng.uniform(0.5, 1.5, n)
+    fixed = np.zeros(n, bool)
+    fixed[:2] = True
+    return x0, mass, fixed, ext, ke, bend, kb
+
+
+def test_forces_match_oracle():
+    x0, mass, fixed, ext, ke, bend, kb = random_network()
+    net = OM.Network(x0, mass, fixed, ext, ke, bend, kb)
+    ms = MassSpring(x0, mass, ext, ke, bend, kb, fixed=fixed)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        x = x0 + 0.02 * rng.normal(size=x0.shape)
+        want = net.forces(x)
+        got = ms.forces(x)
+        assert np.max(np.abs(got - want)) < 1e-7 * np.max(np.abs(want))
+    assert np.max(np.abs(ms.forces(x0))) < 1e-12
+
+
+def test_bdf2_trajectory_matches_oracle_in_moving_frame():
+    """Five variable steps under a tip load in a spinning, accelerating
+    frame: positions and velocities agree with the oracle's BDF2."""
+    x0, mass, fixed, ext, ke, bend, kb = random_network(seed=11)
+    net = OM.Network(x0, mass, fixed, ext, ke, bend, kb)
+    ms = MassSpring(x0, mass, ext, ke, bend, kb, fixed=fixed)
+    fe = np.zeros_like(x0)
+    fe[-1] = (0.0, -0.5, 0.8)
+    x, v = x0.copy(), np.zeros_like(x0)
+    xm1 = vm1 = None
+    dts = [2e-2, 3e-2, 2e-2, 1.5e-2, 2.5e-2]
+    t, dprev = 0.0, None
+    for dt in dts:
+        t += dt
+        fr = dict(A_O=(0.1, 0.0, -0.2), Omega=(0.3 * t, -0.1, 1.0), dOmega=(0.3, 0.0, 0.0))
+        xn, vn, _ = OM.bdf2_step(net, x, v, xm1, vm1, dt, dprev, fe, tol=1e-12, frame=fr)
+        xm1, vm1, x, v, dprev = x, v, xn, vn, dt
+        it = ms.step(dt, fe, frame=fr, tol=1e-12)
+        assert 1 <= it <= 10
+    gx, gv = ms.state()
+    assert np.max(np.abs(gx - x)) < 1e-8 * np.max(np.abs(x))
+    assert np.max(np.abs(gv - v)) < 1e-6 * np.max(np.abs(v))
+    assert np.all(gx[:2] == x0[:2]) and np.all(gv[:2] == 0)
+
+
+def test_equilibrium_matches_oracle():
+    npts = 12
+    net = OM.cantilever(0.3, 0.24, npts, ke=1e7)
+    fe = np.zeros((npts, 3))
+    fe[-1, 1] = -7.84
+    want = OM.equilibrium(net, fe, steps=8, tol=1e-12)
+    ms = cantilever(0.3, 0.24, npts, 1e7)
+    ms.equilibrium(fe, load_steps=8, tol=1e-12)
+    got, v = ms.state()
+    assert np.max(np.abs(got - want)) < 1e-8
+    assert np.all(v == 0)
+
+
+def test_large_deflection_table_at_64_points():
+    """Sec. 2.4.1, Table 1 with the paper's 64 mass points: the tip agrees
+    with the paper's own mass-spring column to 0.3 % plus half a printed
+    unit, and with the continuum beam to the paper's 1 %."""
+    for F, xr, yr, xm, ym in np.loadtxt(GOLDEN):
+        ms = cantilever(0.3, 0.24, 64, 1e7)
+        fe = np.zeros((64, 3))
+        fe[-1, 1] = -F
+        ms.equilibrium(fe, load_steps=8)
+        x, _ = ms.state()
+        dx, dy = x[-1, 0] * 100, x[-1, 1] * 100
+        assert abs(dx - xm) <= 3e-3 * abs(xm) + 5e-3, (F, dx, xm)
+        assert abs(dy - ym) <= 3e-3 * abs(ym) + 5e-3, (F, dy, ym)
+        assert abs(dx - xr) < 1e-2 * abs(xr) and abs(dy - yr) < 1e-2 * abs(yr), (F, dx, dy)
+
+
+def test_moving_frame_closed_form_and_order():
+    """Free particles in a spinning, accelerating frame (no springs) follow
+    R^T (X0 + V0 t - X_O) to second order."""
+    x0 = np.array([[0.4, 0.1, -0.2], [-0.3, 0.5, 0.25]])
+    v_in = np.array([[0.2, -0.1, 0.3], [0.0, 0.4, -0.2]])
+    acc, tau = np.array([0.3, -0.2, 0.1]), 0.5
+
+    def frame(t):
+        phi = tau * math.exp(-t / tau) + t - tau
+        c, s = math.cos(phi), math.sin(phi)
+        R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+        fr = dict(A_O=R.T @ acc, Omega=(0.0, 0.0, 1.0 - math.exp(-t / tau)),
+                  dOmega=(0.0, 0.0, math.exp(-t / tau) / tau))
+        return R, 0.5 * acc * t * t, fr
+
+    errs = []
+    for m in (50, 100, 200):
+        ms = MassSpring(x0, [1.0, 2.5], np.zeros((0, 2), int), [], v0=v_in)
+        for k in range(m):
+            ms.step(1.0 / m, frame=frame((k + 1) / m)[2], tol=1e-13)
+        x, _ = ms.state()
+        R, XO, _ = frame(1.0)
+        errs.append(np.max(np.abs(x - (x0 + v_in - XO[None]) @ R)))
+    assert errs[2] < 1e-4 and 3.6 < errs[0] / errs[1] < 4.4 and 3.8 < errs[1] / errs[2] < 4.2, errs
+
+
+def test_banded_order_keeps_bandwidth_small():
+    """A 20 x 12 membrane grid: the reverse Cuthill--McKee order gives a
+    node bandwidth near the short side, not the node count."""
+    nx, ny = 20, 12
+    x0 = np.array([(i * 0.05, j * 0.05, 0.0) for i in range(nx) for j in range(ny)])
+    ext = []
+    for i in range(nx):
+        for j in range(ny):
+            a = i * ny + j
+            if j + 1 < ny:
+                ext.append((a, a + 1))
+            if i + 1 < nx:
+                ext.append((a, a + ny))
+            if i + 1 < nx and j + 1 < ny:
+                ext.append((a, a + ny + 1))
+    fixed = np.zeros(nx * ny, bool)
+    fixed[:ny] = True
+    ms = MassSpring(x0, 1.0, ext, 100.0, fixed=fixed)
+    nf, bw = ms.info()
+    assert nf == (nx - 1) * ny and bw <= ny + 2
+    # a pull on the far edge: a BDF2 step converges in a few Newton iterations
+    fe = np.zeros_like(x0)
+    fe[-ny:, 2] = 0.1
+    assert ms.step(1e-2, fe, tol=1e-6) <= 4
+
+
+def test_rejects_bad_arguments():
+    x0 = np.zeros((3, 3))
+    x0[:, 0] = (0.0, 1.0, 2.0)
+    with pytest.raises(B.PsError) as e:
+        MassSpring(x0, 1.0, [(0, 3)], 1.0)
+    assert e.value.status == B.PS_EINVAL
+    with pytest.raises(B.PsError):
+        MassSpring(x0, [1.0, 0.0, 1.0], [(0, 1)], 1.0)
+    with pytest.raises(B.PsError):
+        MassSpring(x0, 1.0, [(0, 1)], 1.0, bend=[(0, 1, 1)], kb=1.0)
+    ms = MassSpring(x0, 1.0, [(0, 1), (1, 2)], 1.0)
+    with pytest.raises(B.PsError):
+        ms.step(-1.0)

@@ -132,3 +132,48 @@ def test_first_step_is_backward_euler():
     assert xn[1, 0] - 1.0 == pytest.approx(x1, rel=1e-8)
     assert vn[1, 0] == pytest.approx(-4.0 * dt * x1, rel=1e-8)
     assert np.all(xn[0] == net.x0[0]) and np.all(vn[0] == 0)
+
+
+def _spin_frame(t, tau=0.5, acc=(0.3, -0.2, 0.1)):
+    """Frame turning about z by phi(t) = tau e^{-t/tau} + t - tau (the
+    startup of Sec. 4.2) with its origin accelerating uniformly by acc
+    (inertial axes). Returns R, X_O and the frame's A_O, Omega, dOmega in
+    its own axes."""
+    phi = tau * math.exp(-t / tau) + t - tau
+    w = 1.0 - math.exp(-t / tau)
+    dw = math.exp(-t / tau) / tau
+    c, s = math.cos(phi), math.sin(phi)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    a = np.asarray(acc)
+    return R, 0.5 * a * t * t, dict(A_O=R.T @ a, Omega=(0.0, 0.0, w), dOmega=(0.0, 0.0, dw))
+
+
+def _free_particles():
+    x0 = np.array([[0.4, 0.1, -0.2], [-0.3, 0.5, 0.25]])
+    v_in = np.array([[0.2, -0.1, 0.3], [0.0, 0.4, -0.2]])
+    net = M.Network(x0, [1.0, 2.5], [False, False], np.zeros((0, 2), int), [], np.zeros((0, 3), int), [])
+    return net, x0, v_in
+
+
+def _moving_frame_error(m, T=1.0):
+    net, x0, v_in = _free_particles()
+    x, v = x0.copy(), v_in.copy()   # at t = 0 the frames coincide and Omega = 0
+    xm1 = vm1 = None
+    dt = T / m
+    for k in range(m):
+        _, _, fr = _spin_frame((k + 1) * dt)
+        xn, vn, _ = M.bdf2_step(net, x, v, xm1, vm1, dt, dt, np.zeros_like(x), tol=1e-13, frame=fr)
+        xm1, vm1, x, v = x, v, xn, vn
+    R, XO, _ = _spin_frame(T)
+    want = (x0 + v_in * T - XO[None]) @ R   # rows: R^T (X - X_O)
+    return np.max(np.abs(x - want))
+
+
+def test_moving_frame_free_particle_second_order():
+    """Free particles move on straight lines in the inertial frame; solved
+    in a frame that spins up and accelerates, the fictitious forces must
+    reproduce R^T (X0 + V0 t - X_O(t)) to second order in dt (a wrong sign
+    in any of the four terms leaves an O(1) error)."""
+    e = [_moving_frame_error(m) for m in (40, 80, 160)]
+    assert e[2] < 2e-4, e
+    assert 3.5 < e[0] / e[1] < 4.6 and 3.7 < e[1] / e[2] < 4.3, e
