@@ -346,6 +346,32 @@ def run_ours(args, cfg):
                              "note": "static pressure of the state (passes 1-4, Pi_hat, one inverse field) "
                                      "+ delta interpolation and p A/3 loads on the nodes"}
     del pfield
+    if args.fsi and world == 1:
+        # staggered FSI step (fluid step, pressure, loads, host mass-spring
+        # step, rasterised mask of the new nodes) with an 833-node network
+        from paper_2002_08642_gb300.fsi import FSI
+        from paper_2002_08642_gb300.massspring import MassSpring
+
+        wf = inputs.fsi_wing(ns=48, nc=16, veins=(0, 4, 8, 12, 16))
+        msn = MassSpring(wf["x0"], wf["mass"], wf["ext"], wf["ke"], wf["bend"], wf["kb"], fixed=wf["fixed"])
+        cpl = FSI(g, msn, wf["tri"], lambda t: inputs.revolving_frames(t, centre=(L / 2, L / 2, L / 2)),
+                  tol=1e-8)
+        cpl.step(2)
+        torch.cuda.synchronize()
+        kf = max(3, args.steps // 4)
+        cpl.host_solid_s = 0.0
+        it0 = len(cpl.newton_iters)
+        t0 = time.perf_counter()
+        cpl.step(kf)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / kf
+        out["fsi_step"] = {"value": n ** 3 / wall / 1e6, "unit": "Mpts*steps/s", "ms_per_step": wall * 1e3,
+                           "steps": kf, "nodes": msn.n, "bandwidth": msn.info()[1], "factorizations": msn.info()[2],
+                           "host_solid_ms_per_step": cpl.host_solid_s * 1e3 / kf,
+                           "newton_iters": cpl.newton_iters[it0:],
+                           "note": "wall clock per coupled step: GPU step + pressure + loads (D2H) + host "
+                                   "mass-spring BDF2/Newton + H2D nodes + GPU rasterise"}
+        del cpl, msn
     del g
     torch.cuda.empty_cache()
     if args.fp64 and world == 1:
@@ -449,6 +475,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-256", dest="small", action="store_false")
+    ap.add_argument("--no-fsi", dest="fsi", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -303,8 +303,9 @@ ps_status ps_ms_create(int32_t n_nodes, const double* mass, const double* x0, co
                        int32_t n_bend, const int32_t* bend_ijk, const double* kb, ps_ms** out);
 ps_status ps_ms_destroy(ps_ms* m);
 
-/* Free-node count and the node bandwidth of the Newton matrix. */
-ps_status ps_ms_info(const ps_ms* m, int32_t* n_free, int32_t* bandwidth);
+/* Free-node count, the node bandwidth of the Newton matrix and how many
+ * times a Newton matrix has been built and factored (outputs may be NULL). */
+ps_status ps_ms_info(const ps_ms* m, int32_t* n_free, int32_t* bandwidth, int64_t* factorizations);
 
 /* Internal spring forces at positions x (n_nodes x 3) into f_out. */
 ps_status ps_ms_forces(const ps_ms* m, const double* x, double* f_out);
@@ -321,8 +322,12 @@ ps_status ps_ms_set_state(ps_ms* m, const double* x, const double* v);
  * is backward Euler). f_ext (n_nodes x 3, NULL = 0) is the external force
  * held over the step; frame (NULL = inertial) adds the fictitious forces
  * at the new time level. Newton--Raphson on the positions (velocities
- * eliminated), starting from the current state, until the L2 norm of the
- * update is below tol * max(1, |x|). Returns the iterations in *iters_out
+ * eliminated), starting from the current state. The factored Newton matrix
+ * of an earlier iteration or step is reused while the iteration contracts
+ * by at least 1/2 per iteration and c dt (c = (1+xi)/(1+2xi)) is within
+ * 20 % of the one it was built for; otherwise it is rebuilt at the current
+ * iterate. Converged when the update (times rate/(1 - rate) once a rate is
+ * known) is below tol * max(1, |x|) in L2. Returns the iterations in *iters_out
  * (may be NULL). PS_ENUMERIC, state unchanged, if Newton does not converge
  * in max_iter iterations or its matrix is singular. */
 ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame* frame, double tol,

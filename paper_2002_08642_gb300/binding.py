@@ -76,7 +76,7 @@ _SIGS = {
     "ps_ms_create": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                                c_int32, c_void_p, c_void_p, _P(c_void_p)]),
     "ps_ms_destroy": (c_int32, [c_void_p]),
-    "ps_ms_info": (c_int32, [c_void_p, _P(c_int32), _P(c_int32)]),
+    "ps_ms_info": (c_int32, [c_void_p, _P(c_int32), _P(c_int32), _P(ctypes.c_int64)]),
     "ps_ms_forces": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ps_ms_state": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ps_ms_set_state": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -293,9 +293,9 @@ def ps_ms_destroy(m):
 
 
 def ps_ms_info(m):
-    nf, bw = c_int32(0), c_int32(0)
-    ms_check(lib().ps_ms_info(m, ctypes.byref(nf), ctypes.byref(bw)), m)
-    return nf.value, bw.value
+    nf, bw, nfac = c_int32(0), c_int32(0), ctypes.c_int64(0)
+    ms_check(lib().ps_ms_info(m, ctypes.byref(nf), ctypes.byref(bw), ctypes.byref(nfac)), m)
+    return nf.value, bw.value, nfac.value
 
 
 def ps_ms_forces(m, x_ptr, f_ptr):

@@ -152,6 +152,9 @@ struct ps_ms {
     double dt_prev = 0.0;
     long steps = 0;
     Band J;
+    bool j_valid = false;    // J holds a factored step matrix
+    double j_cdt = 0.0;      // c dt it was built for
+    long factorizations = 0;
     std::string err;
 
     // internal forces F = -grad E at positions y (3 n)
@@ -338,10 +341,11 @@ ps_status ps_ms_destroy(ps_ms* m) {
     return PS_OK;
 }
 
-ps_status ps_ms_info(const ps_ms* m, int32_t* n_free, int32_t* bandwidth) {
+ps_status ps_ms_info(const ps_ms* m, int32_t* n_free, int32_t* bandwidth, int64_t* factorizations) {
     if (!m) return PS_EINVAL;
     if (n_free) *n_free = m->nfree;
     if (bandwidth) *bandwidth = m->bw;
+    if (factorizations) *factorizations = m->factorizations;
     return PS_OK;
 }
 
@@ -367,6 +371,7 @@ ps_status ps_ms_set_state(ps_ms* m, const double* x, const double* v) {
         if (m->fixed[i])
             for (int c = 0; c < 3; ++c) m->v[3 * i + c] = 0.0;
     m->steps = 0;
+    m->j_valid = false;
     return PS_OK;
 }
 
@@ -402,8 +407,46 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
     }
     const int mf = 3 * m->nfree;
     std::vector<double> y(m->x), F(n3), r(mf);
+    // Newton matrix I/cdt - (cdt/m) dF/dy + cdt G + 2 W at y, factored
+    auto build = [&]() -> bool {
+        m->band_reset();
+        m->add_stiffness(y.data());
+        Band& Jb = m->J;
+        for (int i = 0; i < n; ++i) {
+            const int p = m->pos[i];
+            if (p < 0) continue;
+            const double s = -cdt / m->mass[i];
+            for (int q = 0; q < 3; ++q) {
+                const int row = 3 * p + q;
+                const int c0 = std::max(0, row - Jb.kl), c1 = std::min(Jb.m - 1, row + Jb.ku);
+                for (int col = c0; col <= c1; ++col) Jb.at(row, col) *= s;
+                Jb.at(row, row) += 1.0 / cdt;
+                if (frame)
+                    for (int t = 0; t < 3; ++t) Jb.add(row, 3 * p + t, cdt * G[q][t] + 2.0 * W[q][t]);
+            }
+        }
+        m->factorizations++;
+        m->j_cdt = cdt;
+        m->j_valid = Jb.factor();
+        return m->j_valid;
+    };
+    // Simplified Newton: the factored matrix of an earlier iteration or step
+    // is reused while the iteration contracts fast (rate <= 1/2); otherwise,
+    // or when c dt changed by more than 20 %, it is rebuilt at the current
+    // iterate and the iteration goes on from there. Converged when the
+    // update, scaled by rate/(1 - rate) once a rate is known (the remaining
+    // error of a linearly converging iteration), is below tol * max(1, |y|).
+    bool fresh = false;
+    if (!m->j_valid || fabs(cdt / m->j_cdt - 1.0) > 0.2) {
+        if (!build()) {
+            m->err = "ps_ms_step: singular Newton matrix";
+            return PS_ENUMERIC;
+        }
+        fresh = true;
+    }
     int it = 0;
     bool conv = false;
+    double dn_prev = -1.0;
     for (it = 1; it <= max_iter; ++it) {
         // residual of the velocity equation with v = (y - hx)/cdt, on free coordinates
         m->forces(y.data(), F.data());
@@ -422,28 +465,21 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
                 r[3 * p + q] = -(vy[q] - hv[3 * i + q] - cdt * fi / m->mass[i]);
             }
         }
-        // Newton matrix I/cdt - (cdt/m) dF/dy (+ cdt G + 2 W from the frame terms)
-        m->band_reset();
-        m->add_stiffness(y.data());
-        Band& Jb = m->J;
-        for (int i = 0; i < n; ++i) {
-            const int p = m->pos[i];
-            if (p < 0) continue;
-            const double s = -cdt / m->mass[i];
-            for (int q = 0; q < 3; ++q) {
-                const int row = 3 * p + q;
-                const int c0 = std::max(0, row - Jb.kl), c1 = std::min(Jb.m - 1, row + Jb.ku);
-                for (int col = c0; col <= c1; ++col) Jb.at(row, col) *= s;
-                Jb.at(row, row) += 1.0 / cdt;
-                if (frame)
-                    for (int t = 0; t < 3; ++t) Jb.add(row, 3 * p + t, cdt * G[q][t] + 2.0 * W[q][t]);
+        m->J.solve(r.data());
+        const double dn = norm2(r);
+        if (!(dn == dn)) break;
+        const double rate = dn_prev > 0.0 ? dn / dn_prev : -1.0;
+        if (rate > 0.5 && !fresh) {
+            // too slow with the old matrix: rebuild at y and take this iteration again
+            if (!build()) {
+                m->err = "ps_ms_step: singular Newton matrix";
+                return PS_ENUMERIC;
             }
+            fresh = true;
+            dn_prev = -1.0;
+            continue;
         }
-        if (!Jb.factor()) {
-            m->err = "ps_ms_step: singular Newton matrix";
-            return PS_ENUMERIC;
-        }
-        Jb.solve(r.data());
+        if (rate >= 1.0) break;   // diverging even with a fresh matrix
         double yn = 0.0;
         for (int i = 0; i < n; ++i) {
             const int p = m->pos[i];
@@ -453,12 +489,12 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
                 yn += y[3 * i + q] * y[3 * i + q];
             }
         }
-        const double dn = norm2(r);
-        if (!(dn == dn)) break;
-        if (dn < tol * fmax(1.0, sqrt(yn))) {
+        const double est = rate > 0.0 ? dn * rate / (1.0 - rate) : dn;
+        if (est < tol * fmax(1.0, sqrt(yn)) && (rate > 0.0 || fresh)) {
             conv = true;
             break;
         }
+        dn_prev = dn;
     }
     if (iters_out) *iters_out = conv ? it : max_iter;
     if (!conv) {
@@ -493,6 +529,7 @@ ps_status ps_ms_equilibrium(ps_ms* m, const double* f_ext, int32_t load_steps, d
             }
             m->band_reset();
             m->add_stiffness(x.data());
+            m->factorizations++;
             if (!m->J.factor()) {
                 m->err = "ps_ms_equilibrium: singular stiffness";
                 if (iters_out) *iters_out = total;
@@ -524,6 +561,7 @@ ps_status ps_ms_equilibrium(ps_ms* m, const double* f_ext, int32_t load_steps, d
     m->x = x;
     m->v.assign(n3, 0.0);
     m->steps = 0;
+    m->j_valid = false;
     if (iters_out) *iters_out = total;
     return PS_OK;
 }

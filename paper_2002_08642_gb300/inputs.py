@@ -156,3 +156,65 @@ def revolving_wing(t, xw0, a, centre=(2.0, 2.0, 2.0), omega=1.0, pitch_deg=45.0,
     phi, rate = revolving_angle(t, omega, tau)
     R = rot_z(phi) @ rot_y(pitch_deg)
     return xw, vw, frame(R, centre, (0.0, 0.0, 0.0), (0.0, 0.0, rate))
+
+
+# Wing frame of the mass-spring wing: span along wing x (the bending angles
+# of the network are measured in the x-y and x-z planes, so veins run along
+# x), chord along wing y, normal along wing z. P maps the revolving wing's
+# axes (span along y) to these; R_fsi = R P^T keeps the global placement.
+_P_FSI = np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, -1.0]])
+
+
+def fsi_wing(ns=24, nc=8, span=1.0, half_chord=0.175, veins=(0, 4, 8), kb=1.1, ke=200.0, mass=0.281):
+    """Structured mass-spring wing (synthetic recipe in the spirit of the
+    vein/membrane model of Sec. 2.3): stations x_i = i span/ns (i = 0..ns),
+    chordwise points y_ij = c(x_i) (2 j/nc - 1) (j = 0..nc) with
+    c(x) = half_chord (0.35 + 0.65 sqrt(1 - (x/span)^2)); each quad split in
+    two triangles. Membrane: an extension spring of stiffness ke on every
+    triangle edge. Veins: the spanwise lines j in ``veins`` get bending
+    springs of stiffness kb on consecutive triples (kb = 1.1 is what Eq.
+    EI_k_relation gives for EI = 0.05 over 23 points of unit length; the
+    caller converts). Stations 0 and 1 are clamped (the first two
+    points of every vein, as in the cantilever of Sec. 2.3.1). The mass is
+    spread equally over the nodes.
+    Returns dict(x0, tri, ext, ke, bend, kb, mass, fixed)."""
+    n_i, n_j = ns + 1, nc + 1
+    xs = np.linspace(0.0, span, n_i)
+    c = half_chord * (0.35 + 0.65 * np.sqrt(np.clip(1.0 - (xs / span) ** 2, 0.0, 1.0)))
+    x0 = np.zeros((n_i * n_j, 3))
+    for i in range(n_i):
+        x0[i * n_j:(i + 1) * n_j, 0] = xs[i]
+        x0[i * n_j:(i + 1) * n_j, 1] = c[i] * (2.0 * np.arange(n_j) / nc - 1.0)
+    tri = []
+    for i in range(ns):
+        for j in range(nc):
+            a, b = i * n_j + j, (i + 1) * n_j + j
+            tri.append((a, b, b + 1))
+            tri.append((a, b + 1, a + 1))
+    tri = np.asarray(tri, dtype=np.int32)
+    edges = set()
+    for t in tri:
+        for u, v in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0])):
+            edges.add((min(u, v), max(u, v)))
+    ext = np.asarray(sorted(edges), dtype=np.int32)
+    bend = []
+    for j in veins:
+        bend += [(i * n_j + j, (i + 1) * n_j + j, (i + 2) * n_j + j) for i in range(ns - 1)]
+    bend = np.asarray(bend, dtype=np.int32).reshape(-1, 3)
+    fixed = np.zeros(n_i * n_j, dtype=bool)
+    fixed[:2 * n_j] = True
+    return {"x0": x0, "tri": tri, "ext": ext, "ke": np.full(len(ext), float(ke)), "bend": bend,
+            "kb": np.full(len(bend), float(kb)), "mass": np.full(n_i * n_j, mass / (n_i * n_j)), "fixed": fixed}
+
+
+def revolving_frames(t, centre=(2.0, 2.0, 2.0), omega=1.0, pitch_deg=45.0, tau=None):
+    """Frames of the mass-spring wing revolving about global z through
+    ``centre`` (the hinge) at angle phi(t) (``revolving_angle``), pitched
+    about the span axis. Returns (frame for the rasteriser and the loads,
+    frame of the network: A_O, Omega, dOmega in wing axes)."""
+    phi, rate = revolving_angle(t, omega, tau)
+    R = rot_z(phi) @ rot_y(pitch_deg) @ _P_FSI.T
+    acc = 0.0 if tau is None else omega * math.exp(-t / tau) / tau
+    Om = np.array([0.0, 0.0, rate])
+    ms = {"A_O": (0.0, 0.0, 0.0), "Omega": R.T @ Om, "dOmega": R.T @ np.array([0.0, 0.0, acc])}
+    return frame(R, centre, (0.0, 0.0, 0.0), Om), ms

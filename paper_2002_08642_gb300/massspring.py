@@ -51,7 +51,7 @@ class MassSpring:
             pass
 
     def info(self):
-        """(free nodes, node bandwidth of the Newton matrix)."""
+        """(free nodes, node bandwidth of the Newton matrix, matrices factored)."""
         return B.ps_ms_info(self._m)
 
     def forces(self, x):

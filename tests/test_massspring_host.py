@@ -149,7 +149,7 @@ def test_banded_order_keeps_bandwidth_small():
     fixed = np.zeros(nx * ny, bool)
     fixed[:ny] = True
     ms = MassSpring(x0, 1.0, ext, 100.0, fixed=fixed)
-    nf, bw = ms.info()
+    nf, bw, _ = ms.info()
     assert nf == (nx - 1) * ny and bw <= ny + 2
     # a pull on the far edge: a BDF2 step converges in a few Newton iterations
     fe = np.zeros_like(x0)
