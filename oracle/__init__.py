@@ -24,6 +24,13 @@ interaction solver: application to flexible revolving wings"):
 * ``adjoint``  -- the discrete adjoint of ``step`` (no counterpart in the
                   paper; written as the exact transpose of the step's linear
                   algebra).
+* ``pressure`` -- the static pressure of the rotational form and the pressure
+                  loads on the wing's mass points (Sec. 4.1).
+* ``massspring`` -- the mass-spring network: extension and bending springs,
+                  the k^b - EI relation, variable-step BDF2 with Newton, static
+                  equilibrium, moving-frame forces (Sec. 2.1-2.4).
+* ``fsi``      -- the staggered fluid-structure coupling composed of the
+                  modules above (Sec. 4.1, coupling paragraph).
 
 All arithmetic is numpy float64 / complex128. Readings of points the paper
 leaves open are stated at the routine that takes them.
