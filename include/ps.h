@@ -262,6 +262,14 @@ ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision, double L, 
 /* Text of the last error on this context ("" if none). */
 const char* ps_last_error(const ps_ctx* ctx);
 
+/* Measured fused multiply-add rate of the current device in FLOP/s (an FMA
+ * counts 2), PS_FP32 or PS_FP64: 8 blocks of 256 threads per SM, each thread
+ * 8 independent FMA chains of `iters` steps, timed with CUDA events on
+ * cuda_stream after one warm-up launch. Synchronises. It is the arithmetic
+ * ceiling the FP64 step is measured against (no counterpart in the paper).
+ * PS_EINVAL for a bad precision or iters < 1; PS_ECUDA if a launch fails. */
+ps_status ps_fma_peak(int32_t precision, int32_t iters, void* cuda_stream, double* flops_per_s);
+
 /* ------------------------------------------------------------------------
  * Mass-spring network of the wing (Sec. 2.1-2.2). Host code, host memory,
  * double precision; no CUDA call. Node arrays are n_nodes x 3, row-major.

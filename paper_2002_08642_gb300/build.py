@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libps.so")
-SOURCES = ["ps_api.cu", "ps_f32.cu", "ps_f64.cu", "ps_noalloc.cu", "ps_massspring.cu"]
+SOURCES = ["ps_api.cu", "ps_f32.cu", "ps_f64.cu", "ps_noalloc.cu", "ps_massspring.cu", "ps_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]

@@ -23,6 +23,16 @@ def test_algorithmic_bytes_model():
     assert max(ab, key=ab.get) == "y_inverse"
 
 
+def test_step_flop_model():
+    """5 m log2 m FLOPs per complex line transform: at 64^3 (K = 43, Kz = 22)
+    the passes transform 5*43*22 + 6*64*22 + 4.5*64^2 + 3*64*22 + 3*43*22
+    lines of length 64 (5*64*6 = 1920 FLOPs each), plus 15 FLOPs per point."""
+    lines = 5 * 43 * 22 + 6 * 64 * 22 + 4.5 * 64 * 64 + 3 * 64 * 22 + 3 * 43 * 22
+    assert bench.step_flops(64) == pytest.approx(lines * 1920 + 15 * 64 ** 3, rel=1e-12)
+    # about 460 FLOPs per point at 768^3: FP64 at ~1 TFLOP/s is far from HBM-bound
+    assert 440 < bench.step_flops(768) / 768 ** 3 < 480
+
+
 def test_traffic_figure_tracks_kernel_sources(monkeypatch):
     got = bench.measured_traffic("z_c2r_nonlinear_r2c", 768)
     assert got is None or got > 1e10
