@@ -71,6 +71,14 @@ enum { PS_MEAN_FIXED = 0, PS_MEAN_FREE = 1 };
  *              time step (all > 0).
  *   tw, h      wing semi-thickness and smoothing semi-width of the mask.
  *   x0         reference point of the moment.
+ *   keep_uw    1: the workspace also holds three z-spectral fields
+ *              (3 n^2 Kzp complex, Kzp = (n-1)/3 + 1 rounded up to 16 (FP32)
+ *              or 8 (FP64) values) so that ps_pressure keeps u and omega of the
+ *              state it evaluated; a ps_step right after it (nothing between
+ *              that changes the velocity) then starts at its z pass and skips
+ *              the x- and y-inverse passes. This is the staggered coupling's
+ *              order (fluid step, pressure, solid, mask, fluid step).
+ *              0: no extra memory, every step runs all passes.
  */
 typedef struct {
     int32_t n;
@@ -81,6 +89,7 @@ typedef struct {
     double L, nu, eta, dt;
     double tw, h;
     double x0[3];
+    int32_t keep_uw;
 } ps_params;
 
 /* Wing frame -> global frame (Sec. 4.1, Eq. relative_velocities):
@@ -171,7 +180,10 @@ ps_status ps_set_sponge(ps_ctx* ctx, const void* chi_sp_dev, double c_sp);
  *   p_dev  caller-owned n^3 array [x][y][z] in the context precision.
  * Costs about one time step (the step's passes 1-4, then one inverse
  * field). Leaves the state and the forces of ps_forces unchanged; uses the
- * internal scratch arrays. Asynchronous. PS_ESTATE without a velocity. */
+ * internal scratch arrays. With keep_uw the x and y passes it ran are not
+ * repeated by the next ps_step (or a second ps_pressure) on the same state;
+ * the results are the same bits either way. Asynchronous. PS_ESTATE without
+ * a velocity. */
 ps_status ps_pressure(ps_ctx* ctx, void* p_dev);
 
 /* Pressure loads on the wing's mass points (Sec. 4.1, coupling paragraph):

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "P
 class PsParams(ctypes.Structure):
     _fields_ = [("n", c_int32), ("precision", c_int32), ("mask_profile", c_int32), ("mean_mode", c_int32),
                 ("with_adjoint", c_int32), ("L", c_double), ("nu", c_double), ("eta", c_double), ("dt", c_double),
-                ("tw", c_double), ("h", c_double), ("x0", c_double * 3)]
+                ("tw", c_double), ("h", c_double), ("x0", c_double * 3), ("keep_uw", c_int32)]
 
 
 class PsFrame(ctypes.Structure):

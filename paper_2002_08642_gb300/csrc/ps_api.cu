@@ -47,6 +47,8 @@ struct ps_ctx {
     CUtensorMap tmG;          // adjoint G (x-inverse input), with_adjoint only
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
     CUtensorMap tmBo;         // B in y-forward boxes of the slab pipeline
+    CUtensorMap tmN;          // keep_uw: the pressure's N fields (y-forward input)
+    bool uw_valid;            // keep_uw: B holds u and omega of the current state
     // adjoint (with_adjoint): lam, mu, G, W, Ub, Wb spectral; u, w, nb physical
     void* adj_spec[6];
     void* adj_phys[3];
@@ -74,7 +76,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int tile_width(int fp64) { return fp64 ? 8 : 16; }
 
 struct Layout {
-    size_t U, H, A, B, chi, us, flag, tw, Ex, Ez, partial, out, err, mask, adj_spec[6], adj_phys[3], gX, total;
+    size_t U, H, A, B, N3, chi, us, flag, tw, Ex, Ez, partial, out, err, mask, adj_spec[6], adj_phys[3], gX, total;
     size_t ustate, mask_bytes;
 };
 
@@ -95,6 +97,7 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->H = take(L->ustate);
     L->A = take(6 * (size_t)n * K * Kzp * ec);
     L->B = take(6 * (size_t)n * n * Kzp * ec);
+    L->N3 = p->keep_uw ? take(3 * (size_t)n * n * Kzp * ec) : 0;
     L->chi = take(n3 * er);
     L->us = take(3 * n3 * er);
     L->flag = take((size_t)n * n);
@@ -179,6 +182,7 @@ ps_status check_params(const ps_params* p, std::string* why) {
     if (p->mask_profile != PS_MASK_COS && p->mask_profile != PS_MASK_TANH) { *why = "bad mask_profile"; return PS_EINVAL; }
     if (p->mean_mode != PS_MEAN_FIXED && p->mean_mode != PS_MEAN_FREE) { *why = "bad mean_mode"; return PS_EINVAL; }
     if (p->with_adjoint != 0 && p->with_adjoint != 1) { *why = "with_adjoint must be 0 or 1"; return PS_EINVAL; }
+    if (p->keep_uw != 0 && p->keep_uw != 1) { *why = "keep_uw must be 0 or 1"; return PS_EINVAL; }
     if (!(p->L > 0) || !(p->nu >= 0) || !(p->eta > 0) || !(p->dt > 0) || !(p->h > 0) || !(p->tw >= 0)) {
         *why = "L, eta, dt, h must be > 0 and nu, tw >= 0";
         return PS_EINVAL;
@@ -497,6 +501,9 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     c->b.H = w + L.H;
     c->b.A = w + L.A;
     c->b.B = w + L.B;
+    c->b.N3 = p->keep_uw ? (void*)(w + L.N3) : nullptr;
+    c->b.tmN = nullptr;
+    c->uw_valid = false;
     c->b.chi = w + L.chi;
     c->b.us = w + L.us;
     c->b.flag = (uint8_t*)(w + L.flag);
@@ -554,6 +561,13 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
             }
             c->b.tmG = &c->tmG;
         }
+        if (p->keep_uw) {
+            if (!encode_rows(&c->tmN, c->b.N3, c->fp64, (size_t)3 * n * n, kp.Kzp, ops->cy4, ops->br4)) {
+                delete c;
+                return PS_ECUDA;
+            }
+            c->b.tmN = &c->tmN;
+        }
     }
     if (e != cudaSuccess) { ps_status s = cuda_fail(c, e, "kernel attributes"); delete c; return s; }
     std::vector<unsigned char> tw, ex, ez;
@@ -587,6 +601,7 @@ ps_status ps_destroy(ps_ctx* c) {
 
 ps_status ps_set_velocity(ps_ctx* c, const void* u) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!u) return fail(c, PS_EINVAL, "ps_set_velocity: null u");
     DeviceGuard dg(c->device);
     cudaError_t e = c->ops->set_velocity(c->kp, c->b, u, c->stream);
@@ -598,6 +613,7 @@ ps_status ps_set_velocity(ps_ctx* c, const void* u) {
 
 ps_status ps_get_velocity(ps_ctx* c, void* u) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!u) return fail(c, PS_EINVAL, "ps_get_velocity: null u");
     DeviceGuard dg(c->device);
     cudaError_t e = c->ops->get_velocity(c->kp, c->b, u, c->stream);
@@ -689,7 +705,9 @@ ps_status ps_step(ps_ctx* c, int32_t nsteps) {
     for (int i = 0; i < nsteps; ++i) {
         cudaEvent_t* ev = nullptr;
         if (c->timing) ev = &c->tev_step[(size_t)(c->t_steps++ % kTimingRing) * kEvPerStep];
-        cudaError_t e = c->ops->step(c->kp, c->b, c->nstep == 0, c->stream, ev);
+        const int resume = c->uw_valid ? 1 : 0;
+        c->uw_valid = false;   // the step's z pass overwrites u in B
+        cudaError_t e = c->ops->step(c->kp, c->b, c->nstep == 0, resume, c->stream, ev);
         if (e != cudaSuccess) return cuda_fail(c, e, "ps_step");
         c->nstep++;
     }
@@ -713,8 +731,11 @@ ps_status ps_pressure(ps_ctx* c, void* p_dev) {
     if (!p_dev) return fail(c, PS_EINVAL, "ps_pressure: null output");
     if (!c->has_velocity) return fail(c, PS_ESTATE, "ps_pressure: no velocity set");
     DeviceGuard dg(c->device);
-    cudaError_t e = c->ops->pressure(c->kp, c->b, p_dev, c->stream);
+    const int resume = c->uw_valid ? 1 : 0;
+    c->uw_valid = false;
+    cudaError_t e = c->ops->pressure(c->kp, c->b, p_dev, resume, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ps_pressure");
+    c->uw_valid = c->b.N3 != nullptr;   // keep_uw: B still holds u and omega of the state
     return PS_OK;
 }
 
@@ -808,6 +829,7 @@ ps_status ps_save_state(ps_ctx* c, void* buf) {
 
 ps_status ps_restore_state(ps_ctx* c, const void* buf) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!buf || ((uintptr_t)buf & 15)) return fail(c, PS_EINVAL, "ps_restore_state: null or unaligned buffer");
     DeviceGuard dg(c->device);
     const unsigned char* d = (const unsigned char*)buf;
@@ -826,6 +848,7 @@ ps_status ps_restore_state(ps_ctx* c, const void* buf) {
 
 ps_status ps_adjoint_reset(ps_ctx* c) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!c->p.with_adjoint) return fail(c, PS_ESTATE, "ps_adjoint_reset: context created without with_adjoint");
     DeviceGuard dg(c->device);
     cudaError_t e;
@@ -838,6 +861,7 @@ ps_status ps_adjoint_reset(ps_ctx* c) {
 ps_status ps_adjoint_step(ps_ctx* c, const double dJdF[3], const double dJdM[3], int32_t first, void* grad_chi_dev,
                           void* grad_us_dev) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!c->p.with_adjoint) return fail(c, PS_ESTATE, "ps_adjoint_step: context created without with_adjoint");
     if (!dJdF || !dJdM || !grad_chi_dev || !grad_us_dev)
         return fail(c, PS_EINVAL, "ps_adjoint_step: null argument");
@@ -853,6 +877,7 @@ ps_status ps_adjoint_step(ps_ctx* c, const double dJdF[3], const double dJdM[3],
 
 ps_status ps_mask_nodes_vjp(ps_ctx* c, const void* grad_chi_dev, const void* grad_us_dev, double* grad_xw_dev) {
     if (!c) return PS_EINVAL;
+    c->uw_valid = false;   // overwrites B (or the state it was taken from)
     if (!grad_chi_dev || !grad_us_dev || !grad_xw_dev) return fail(c, PS_EINVAL, "ps_mask_nodes_vjp: null argument");
     if (!c->has_last_mask)
         return fail(c, PS_ESTATE, "ps_mask_nodes_vjp: the current mask did not come from ps_set_mask_from_nodes");

@@ -44,6 +44,8 @@ struct Bufs {
     const CUtensorMap* tmBo; // B, y-forward box of the slab pipeline
     const CUtensorMap* tmG;  // adjoint G as rows of 2 Kzp reals, x-inverse box (null without adjoint)
     const void* chi_sp;      // sponge mask (n^3, caller-owned), null when the sponge term is off
+    void* N3;                // keep_uw: 3 z-spectral fields [f][x][y][kz] for the pressure's N (else null)
+    const CUtensorMap* tmN;  // N3 as rows of 2 Kzp reals (y-forward input), keep_uw only
     cudaStream_t aux[2];     // slab pipeline streams
     cudaEvent_t sev[3];      // fork/join events of the slab pipeline
 };
@@ -62,7 +64,7 @@ struct Ops {
     cudaError_t (*prepare)(int nsm, int* zblocks, int* nslab);
     int nslab;    // slabs of the y/z/y pipeline (set by prepare)
     // ev (nullable): kEvPerStep events (see kEvPerStep)
-    cudaError_t (*step)(const KP&, const Bufs&, int first, cudaStream_t, cudaEvent_t* ev);
+    cudaError_t (*step)(const KP&, const Bufs&, int first, int resume, cudaStream_t, cudaEvent_t* ev);
     cudaError_t (*set_velocity)(const KP&, const Bufs&, const void* u, cudaStream_t);
     cudaError_t (*get_velocity)(const KP&, const Bufs&, void* u, cudaStream_t);
     // generic 3-field transforms between compact spectral arrays (3 x
@@ -74,7 +76,7 @@ struct Ops {
     // physical inverse of the adjoint array G (needs b.tmG)
     cudaError_t (*inv_g)(const KP&, const Bufs&, void* phys, cudaStream_t);
     // static pressure of the state in U with the current mask (n^3 real)
-    cudaError_t (*pressure)(const KP&, const Bufs&, void* p, cudaStream_t);
+    cudaError_t (*pressure)(const KP&, const Bufs&, void* p, int resume, cudaStream_t);
 };
 
 template <typename T, int N> struct Engine {
@@ -213,25 +215,30 @@ template <typename T, int N> struct Engine {
     static int zblocks() { return N * N / GE::LY; }
 
 
-    static cudaError_t step(const KP& kp, const Bufs& b, int first, cudaStream_t s, cudaEvent_t* ev) {
+    // resume: B already holds u and omega of the state (y-inverse output,
+    // left by the pressure evaluation of a keep_uw context), so passes 1 and
+    // 2 are skipped; their timing events are recorded back to back
+    static cudaError_t step(const KP& kp, const Bufs& b, int first, int resume, cudaStream_t s, cudaEvent_t* ev) {
         const C2* tw = (const C2*)b.tw;
         if (ev) cudaEventRecord(ev[0], s);
+        if (!resume) {
 #if PS_X1_OLD
-        k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
+            k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
 #else
-        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
+            k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
 #endif
+        }
         if (ev) cudaEventRecord(ev[1], s);
         const int S = b.chi_sp ? 1 : nslab();   // the sponge variant runs the plain serial passes
         if (b.chi_sp) {
             KP k1 = kp;
             k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
             if (ev) cudaEventRecord(ev[2], s);
-            k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+            if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
             if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
             k_zpass<T, N, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                                      b.flag, b.partial, tw, b.err, nullptr,
-                                                                     (const T*)b.chi_sp);
+                                                                     (const T*)b.chi_sp, (C2*)b.B);
             if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
             k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
             if (ev) cudaEventRecord(ev[7], s);
@@ -246,10 +253,10 @@ template <typename T, int N> struct Engine {
             KP k1 = kp;
             k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
             if (ev) cudaEventRecord(ev[2], s);
-            k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+            if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
             if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
             k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                        b.flag, b.partial, tw, b.err, nullptr, nullptr);
+                                                        b.flag, b.partial, tw, b.err, nullptr, nullptr, (C2*)b.B);
             if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
             k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
             if (ev) cudaEventRecord(ev[7], s);
@@ -266,10 +273,11 @@ template <typename T, int N> struct Engine {
                 k1.part_off = sl * ovl_z();
                 cudaEvent_t* e = ev ? ev + 2 + 6 * sl : nullptr;
                 if (e) cudaEventRecord(e[0], st);
-                k_yinv_tma<T, N><<<ovl_y2(), thr_y2, sm_y2, st>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+                if (!resume) k_yinv_tma<T, N><<<ovl_y2(), thr_y2, sm_y2, st>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
                 if (e) { cudaEventRecord(e[1], st); cudaEventRecord(e[2], st); }
                 k_zpass<T, N><<<ovl_z(), thr_zp, sm_zp, st>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                             b.flag, b.partial, tw, b.err, nullptr, nullptr);
+                                                             b.flag, b.partial, tw, b.err, nullptr, nullptr,
+                                                             (C2*)b.B);
                 if (e) { cudaEventRecord(e[3], st); cudaEventRecord(e[4], st); }
                 k_yfwd_tma<T, N, GE::CY4O><<<ovl_y4(), thr_y4o, sm_y4o, st>>>(*b.tmBo, k1, (C2*)b.A, tw, b.err);
                 if (e) cudaEventRecord(e[5], st);
@@ -344,21 +352,29 @@ template <typename T, int N> struct Engine {
     // mask (n^3, [x][y][z]): the step's passes 1-4 (the z pass also writing
     // (1/2)|u|^2 to p), the x-forward pass writing Pi_hat into A's field 3,
     // then its inverse (x, y, then z pairs of lines: p := Pi - p)
-    static cudaError_t pressure(const KP& kp, const Bufs& b, void* p, cudaStream_t s) {
+    // With b.N3 (keep_uw) the z pass writes N to N3 and the inverse of Pi
+    // runs through A and N3, so B still holds u and omega of the state at
+    // the end: the next step may resume at its z pass. resume: B already
+    // holds them (a second evaluation on the same state), skip passes 1-2.
+    static cudaError_t pressure(const KP& kp, const Bufs& b, void* p, int resume, cudaStream_t s) {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
-        k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        if (!resume) {
+            k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
+            k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        }
+        C2* nout = b.N3 ? (C2*)b.N3 : (C2*)b.B;
         k_zpass<T, N, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
-                                                          b.partial, tw, b.err, (T*)p, nullptr);
-        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+                                                          b.partial, tw, b.err, (T*)p, nullptr, nout);
+        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(b.N3 ? *b.tmN : *b.tmB, k1, (C2*)b.A, tw,
+                                                                  b.err);
         C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * GE::KZP;
         k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
-        k_yinv<T, N, 1><<<grid_ys(k1), thr_s, sm_strided, s>>>(k1, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)p, tw);
+        k_yinv<T, N, 1><<<grid_ys(k1), thr_s, sm_strided, s>>>(k1, (const C2*)b.A, nout, tw);
+        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, tw);
         return cudaGetLastError();
     }
 

@@ -421,7 +421,9 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // holds z[3a + b] at position b M + a, so the pointwise phase reads and
 // writes in place and no reordering pass is needed.
 // PM (pressure evaluation): also writes (1/2)|u|^2 to half_u2 (n^3,
-// [x][y][z]) and leaves the force partials of the last step untouched.
+// [x][y][z]), leaves the force partials of the last step untouched and
+// writes its three result fields to Bo (Bo = B allowed), so that B can keep
+// u and omega of the state for the step that follows.
 // SP (sponge term on): also s = chi_sp omega, transformed forward like n
 // (s_x + i s_y per line by the third thread group, s_z of line pairs by the
 // odd lines' second group, the groups that are otherwise idle) into B
@@ -430,7 +432,7 @@ template <typename T, int N, bool PM = false, bool SP = false>
 __global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
         const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
-        int* __restrict__ err, T* __restrict__ half_u2, const T* __restrict__ chi_sp) {
+        int* __restrict__ err, T* __restrict__ half_u2, const T* __restrict__ chi_sp, cplx<T>* Bo) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LZ = GE::LZ, LP = GE::LP, KZP = GE::KZP;
@@ -665,6 +667,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             __syncthreads();
         }
         // unpack the two-for-one transforms, keep kz < Kz
+        C2* const Bw = PM ? Bo : B;
         for (int idx = threadIdx.x; idx < LZ * Kz; idx += blockDim.x) {
             const int l = idx / Kz, k = idx % Kz;
             const size_t lo = ((size_t)b * LZ + l) * KZP;
@@ -673,11 +676,11 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             const int m = (N - k) % N;
             const C2 zk = t0[zad(k)], zm = t0[zad(m)];
             // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
-            B[lo + k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-            B[BS + lo + k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+            Bw[lo + k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            Bw[BS + lo + k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
             const C2 wk = t1[zad(k)], wm = t1[zad(m)];
-            B[2 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
-                                         : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
+            Bw[2 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
+                                          : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
             if constexpr (SP) {
                 const C2* t2 = tile(l, 2);
                 const C2* t3 = tile(l | 1, 1);

@@ -14,7 +14,7 @@ _MEAN = {"fixed": B.PS_MEAN_FIXED, "free": B.PS_MEAN_FREE}
 
 
 def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                tw=None, h=None, x0=None, with_adjoint=False):
+                tw=None, h=None, x0=None, with_adjoint=False, keep_uw=False):
     dx = L / n
     p = B.PsParams()
     p.n = int(n)
@@ -22,6 +22,7 @@ def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mo
     p.mask_profile = _PROFILE[mask_profile]
     p.mean_mode = _MEAN[mean_mode]
     p.with_adjoint = 1 if with_adjoint else 0
+    p.keep_uw = 1 if keep_uw else 0
     p.L, p.nu, p.eta, p.dt = float(L), float(nu), float(eta), float(dt)
     p.tw = float(2.0 * dx if tw is None else tw)
     p.h = float(1.5 * dx if h is None else h)
@@ -35,11 +36,12 @@ class Solver:
     """One penalized pseudo-spectral solver on one CUDA device."""
 
     def __init__(self, n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                 tw=None, h=None, x0=None, device=None, stream=None, with_adjoint=False):
+                 tw=None, h=None, x0=None, device=None, stream=None, with_adjoint=False, keep_uw=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libps needs a CUDA device")
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0, with_adjoint)
+        self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0, with_adjoint,
+                                  keep_uw)
         self.n = int(n)
         self.L = float(L)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32

@@ -34,8 +34,9 @@ def _setup(n, ns=6, nc=2):
     return L, nu, eta, dt, w, frames, u0
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("fp32", 2e-3)])
-def test_fsi_loop_matches_oracle(prec, tol):
+@pytest.mark.parametrize("prec,tol,keep", [("fp64", 1e-6, False), ("fp32", 2e-3, False), ("fp64", 1e-6, True),
+                                           ("fp32", 2e-3, True)])
+def test_fsi_loop_matches_oracle(prec, tol, keep):
     n, K = 32, 3
     L, nu, eta, dt, w, frames, u0 = _setup(n)
     dx = L / n
@@ -44,7 +45,7 @@ def test_fsi_loop_matches_oracle(prec, tol):
     o = OF.Coupled(p, net, w["tri"], frames, u0, 2 * dx, 1.5 * dx, tol=1e-12)
     o.step(K)
     dtype = torch.float64 if prec == "fp64" else torch.float32
-    g = Solver(n, L, nu, eta, dt, precision=prec, x0=(2.0, 2.0, 2.0))
+    g = Solver(n, L, nu, eta, dt, precision=prec, x0=(2.0, 2.0, 2.0), keep_uw=keep)
     g.set_velocity(torch.from_numpy(u0).to("cuda", dtype))
     ms = MassSpring(w["x0"], w["mass"], w["ext"], w["ke"], w["bend"], w["kb"], fixed=w["fixed"])
     c = FSI(g, ms, w["tri"], frames, tol=1e-12)

@@ -106,3 +106,38 @@ def test_pressure_taylor_green_768_fp32_closed_form():
     print("768^3 TG-3D pressure: max sampled error %.2e" % err)
     assert err < 1e-5
     g.close()
+
+
+@pytest.mark.parametrize("n,prec", [(32, "fp64"), (48, "fp32"), (128, "fp32")])
+def test_keep_uw_resume_is_bitwise_identical(n, prec):
+    """keep_uw: the step after ps_pressure starts at its z pass with the u
+    and omega the pressure left in B. The coupling order (step, pressure,
+    new mask, step, pressure twice, step) gives the same bits as a context
+    that runs every pass (128^3 runs the y/z/y slab pipeline)."""
+    L, nu, eta, dt = 4.0, 1.527e-4, 1e-2, 5e-4
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    xw0, tri = inputs.elliptic_wing_mesh(300)
+    amp = inputs.flapping_amplitudes(xw0)
+    u = inputs.random_field(n, L, seed=n + 13, rms=0.3)
+    res = []
+    for keep in (False, True):
+        g = Solver(n, L, nu, eta, dt, precision=prec, x0=(2.0, 2.0, 2.0), keep_uw=keep)
+        g.set_velocity(dev(u, dtype))
+        for k, t in enumerate((0.3, 0.35)):
+            xw, vw, fr = inputs.revolving_wing(t, xw0, amp)
+            g.set_mask_from_nodes(dev(xw, torch.float64), dev(vw, torch.float64), dev(tri, torch.int32), fr)
+            if k == 0:
+                g.step(2)
+                p1 = g.pressure().clone()
+        g.step(1)
+        F1 = g.forces()
+        p2 = g.pressure().clone()
+        p3 = g.pressure().clone()
+        g.step(1)
+        res.append((p1, p2, p3, F1, g.forces(), g.velocity().clone()))
+        g.close()
+    a, b = res
+    for k in (0, 1, 2, 5):
+        assert torch.equal(a[k], b[k]), k
+    assert a[3] == b[3] and a[4] == b[4]
+    assert torch.equal(b[1], b[2])
