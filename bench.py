@@ -321,6 +321,17 @@ def run_ours(args, cfg):
     step_bytes = sum(ab.values())
     # five passes + rasteriser (clear, nodes, tris, prefix, scatter1, scatter2, eval)
     kernels_per_step = 5 + 7
+    # the z pass against the FP32 FMA rate: its line transforms (4.5 complex
+    # length-n transforms per (x, y) line, 5 n log2 n FLOPs each) and the
+    # pointwise term; it is bound by instruction issue, not by FMA throughput
+    from paper_2002_08642_gb300 import binding as PB
+
+    z_ms = passes["z_c2r_nonlinear_r2c"][0] / max(passes["z_c2r_nonlinear_r2c"][1], 1)
+    peak32 = PB.ps_fma_peak(PB.PS_FP32 if cfg["precision"] == "fp32" else PB.PS_FP64, 200000, stream.cuda_stream)
+    z_fl = 4.5 * n * n * 5.0 * n * math.log2(n) + 15.0 * n ** 3
+    z_pass_alu = {"bound": "alu", "achieved": z_fl / (z_ms / 1e3) / 1e12, "peak": peak32 / 1e12,
+                  "unit": "TFLOP/s", "frac": z_fl / (z_ms / 1e3) / peak32, "flops_per_launch": z_fl,
+                  "peak_source": "measured FMA rate of the path's precision"}
     out = {
         "metric": "Mpts*steps/s", "value": value, "unit": "Mpts*steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -334,6 +345,7 @@ def run_ours(args, cfg):
                      "algorithmic_bytes_per_launch": ab[top]},
         "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                           "achieved_GBs": step_bytes / (ms / args.steps / 1e3) / 1e9},
+        "z_pass_alu": z_pass_alu,
         "passes_ms": {k: v[0] / max(v[1], 1) for k, v in passes.items()},
         "e2e": {"value": e2e, "unit": "Mpts*steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": kernels_per_step * args.steps,
