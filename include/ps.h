@@ -344,9 +344,9 @@ ps_status ps_ms_set_state(ps_ms* m, const double* x, const double* v);
  * at the new time level. Newton--Raphson on the positions (velocities
  * eliminated), starting from the current state. The factored Newton matrix
  * of an earlier iteration or step is reused while the iteration contracts
- * by at least 1/2 per iteration and c dt (c = (1+xi)/(1+2xi)) is within
- * 20 % of the one it was built for; otherwise it is rebuilt at the current
- * iterate. Converged when the update (times rate/(1 - rate) once a rate is
+ * by at least 1/2 per iteration (for at most six iterations) and c dt
+ * (c = (1+xi)/(1+2xi)) is within 20 % of the one it was built for;
+ * otherwise it is rebuilt at the current iterate. Converged when the update (times rate/(1 - rate) once a rate is
  * known) is below tol * max(1, |x|) in L2. Returns the iterations in *iters_out
  * (may be NULL). PS_ENUMERIC, state unchanged, if Newton does not converge
  * in max_iter iterations or its matrix is singular. */

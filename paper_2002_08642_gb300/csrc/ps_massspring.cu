@@ -431,9 +431,9 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
         return m->j_valid;
     };
     // Simplified Newton: the factored matrix of an earlier iteration or step
-    // is reused while the iteration contracts fast (rate <= 1/2); otherwise,
-    // or when c dt changed by more than 20 %, it is rebuilt at the current
-    // iterate and the iteration goes on from there. Converged when the
+    // is reused while the iteration contracts fast (rate <= 1/2, at most six
+    // iterations); otherwise, or when c dt changed by more than 20 %, it is
+    // rebuilt at the current iterate and the iteration goes on from there. Converged when the
     // update, scaled by rate/(1 - rate) once a rate is known (the remaining
     // error of a linearly converging iteration), is below tol * max(1, |y|).
     bool fresh = false;
@@ -469,7 +469,7 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
         const double dn = norm2(r);
         if (!(dn == dn)) break;
         const double rate = dn_prev > 0.0 ? dn / dn_prev : -1.0;
-        if (rate > 0.5 && !fresh) {
+        if (!fresh && (rate > 0.5 || it > 6)) {
             // too slow with the old matrix: rebuild at y and take this iteration again
             if (!build()) {
                 m->err = "ps_ms_step: singular Newton matrix";

@@ -22,7 +22,10 @@ class FSI:
     """Couples a ``Solver`` (GPU) and a ``MassSpring`` network (host).
 
     frames(t) -> (frame dict R, X_O, V_O, Omega for the rasteriser and the
-    loads, frame dict A_O, Omega, dOmega of the network in wing axes)."""
+    loads, frame dict A_O, Omega, dOmega of the network in wing axes).
+    The node copies run on torch's current stream, which must be the
+    solver's stream (the default). A solver created with keep_uw=True
+    skips the x- and y-inverse passes of every step after the first."""
 
     def __init__(self, solver, ms: MassSpring, tri, frames, t0=0.0, tol=1e-8, max_iter=20):
         self.solver = solver
