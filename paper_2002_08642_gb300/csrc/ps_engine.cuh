@@ -182,6 +182,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_xinv_tma<T, N>, sm_x1))) return e;
         if ((e = attr(k_xinv_tma<T, N, 3>, sm_x1))) return e;
         if ((e = attr(k_yinv_tma<T, N, 3>, sm_y2))) return e;
+        if ((e = attr(k_yinv_tma<T, N, 1>, sm_y2))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
@@ -351,7 +352,8 @@ template <typename T, int N> struct Engine {
     // static pressure p = Pi - (1/2)|u|^2 of the state U with the current
     // mask (n^3, [x][y][z]): the step's passes 1-4 (the z pass also writing
     // (1/2)|u|^2 to p), the x-forward pass writing Pi_hat into A's field 3,
-    // then its inverse (x, y, then z pairs of lines: p := Pi - p)
+    // then its inverse (x; y by the TMA-staged pass; z pairs of lines:
+    // p := Pi - p)
     // With b.N3 (keep_uw) the z pass writes N to N3 and the inverse of Pi
     // runs through A and N3, so B still holds u and omega of the state at
     // the end: the next step may resume at its z pass. resume: B already
@@ -373,7 +375,7 @@ template <typename T, int N> struct Engine {
         k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
-        k_yinv<T, N, 1><<<grid_ys(k1), thr_s, sm_strided, s>>>(k1, (const C2*)b.A, nout, tw);
+        k_yinv_tma<T, N, 1><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
         k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, tw);
         return cudaGetLastError();
     }
