@@ -86,9 +86,6 @@ template <typename T, int N> struct Engine {
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
     static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2) / 2;
-    // k_zinv_phys MODE 1: the line tiles plus two transformed lines per group
-    static constexpr size_t sm_z1 =
-        tw_bytes + (size_t)GE::LY * GE::LP * sizeof(C2) + 16 + (size_t)GE::LY * 2 * N * sizeof(T);
     static constexpr size_t sm_zp = (size_t)GE::zsmem(GE::LZ);
     static constexpr int thr_s = GE::C * GE::G;
     static constexpr int thr_5 = GE::C5 * GE::G;
@@ -163,7 +160,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_zpass<T, N, true>, sm_zp))) return e;
         if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
-        if ((e = attr(k_zinv_phys<T, N, 1>, sm_z1))) return e;
+        if ((e = attr(k_zinv_phys<T, N, 1>, sm_z))) return e;
         if ((e = attr(k_zfwd_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
@@ -379,7 +376,7 @@ template <typename T, int N> struct Engine {
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
         k_yinv_tma<T, N, 1><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
-        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z1, s>>>(k1, (const C2*)nout, (T*)p, tw);
+        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, tw);
         return cudaGetLastError();
     }
 

@@ -91,10 +91,6 @@
 #define PS_Y4O_SMEM_KB 120
 #endif
 
-#include <stdint.h>
-
-#include <type_traits>
-
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
 
@@ -1424,9 +1420,7 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
 
 // Inverse: B fields 0..2 (z spectral, kz < Kz) -> physical u (3 x n^3 real).
 // MODE 1: one field, B field 0 -> u[0..n^3) as u := (inverse) - u, each
-// thread group on a pair of lines (launch (zblocks() + 1) / 2 blocks); the
-// two transformed lines go to shared memory first, then u is read and
-// written in 16-byte vectors (the pair is 2n contiguous values of u).
+// thread group on a pair of lines (launch (zblocks() + 1) / 2 blocks).
 template <typename T, int N, int MODE = 0>
 __global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
 k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
@@ -1469,36 +1463,12 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
         const bool on = 2 * lid < (long)N * N;
         const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
         const C2* f0 = B + lo2;
-        // [LY][2n] after the tiles, rounded up to 16 bytes (the launch adds 16)
-        const uintptr_t rb = (reinterpret_cast<uintptr_t>(tiles + LY * LP) + 15u) & ~(uintptr_t)15u;
-        T* res = reinterpret_cast<T*>(rb) + (size_t)line * 2 * N;
         auto load = [&](int q) -> C2 { return two(f0, f0 + Kzp, q); };
         auto store = [&](int z, C2 v) {
-            res[z] = v.x;
-            res[N + z] = v.y;
+            u[po2 + z] = v.x - u[po2 + z];
+            u[po2 + N + z] = v.y - u[po2 + N + z];
         };
         FFT::template run_masked<false>(tiles, tw, addr, g, load, store, on);
-        __syncthreads();
-        if (!on) return;
-        T* up = u + po2;
-        constexpr int V = 16 / (int)sizeof(T);   // values per 16-byte vector
-        if ((reinterpret_cast<uintptr_t>(up) & 15u) == 0) {
-            using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-            Vec* uv = reinterpret_cast<Vec*>(up);
-            const Vec* rv = reinterpret_cast<const Vec*>(res);
-            for (int i = g; i < 2 * N / V; i += G) {
-                Vec h = uv[i];
-                const Vec r = rv[i];
-                if constexpr (sizeof(T) == 4) {
-                    h.x = r.x - h.x; h.y = r.y - h.y; h.z = r.z - h.z; h.w = r.w - h.w;
-                } else {
-                    h.x = r.x - h.x; h.y = r.y - h.y;
-                }
-                uv[i] = h;
-            }
-        } else {
-            for (int i = g; i < 2 * N; i += G) up[i] = res[i] - up[i];
-        }
         return;
     }
     {
