@@ -20,7 +20,7 @@ Follows Sec. 4.1:
   that the projected point and the fluid node share one velocity).
   Node global positions are X_O + R x^(w).
 
-Readings (listed in DESIGN.md): ties in delta go to the smallest triangle id;
+Readings: ties in delta go to the smallest triangle id;
 u_s is set where chi > 0 in the banded (cosine) mode and is 0 elsewhere; the
 alternative tanh profile chi = (1/2)(1 - tanh((delta - t_w)/h)) is evaluated
 at every grid point with the minimum over all triangles.

@@ -13,7 +13,7 @@ total pressure eliminated by the Leray projection P, the spectral form is
     N_hat     = F[ u x omega - (chi/eta)(u - u_s) ]   (omega x u moves to the
                                                        right as +u x omega)
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 
 * Dealiasing: the cubic 2/3 rule -- a mode (m_x, m_y, m_z) is kept iff
   3|m_i| < n on every axis (an integer test). It is applied to the initial
