@@ -170,3 +170,83 @@ def test_rejects_bad_arguments():
     ms = MassSpring(x0, 1.0, [(0, 1), (1, 2)], 1.0)
     with pytest.raises(B.PsError):
         ms.step(-1.0)
+
+
+# --------------------------------------------------------- membrane model
+def _tri_sheet(m):
+    """Regular triangular lattice on about [0, 1]^2: rows along x with
+    spacing a = 1/m, row pitch a sqrt(3)/2, odd rows shifted by a/2; springs
+    between nearest neighbours. Returns nodes, springs, left/right edge
+    nodes per row and the weight (row pitch share) of each row."""
+    a = 1.0 / m
+    h = a * math.sqrt(3) / 2
+    nrow = int(round(1.0 / h)) + 1
+    pts, idx = [], {}
+    for r in range(nrow):
+        for c in range(m + 1 if r % 2 == 0 else m):
+            idx[(r, c)] = len(pts)
+            pts.append(((0.5 * a if r % 2 else 0.0) + c * a, r * h, 0.0))
+    ext = []
+    for (r, c), i in idx.items():
+        nb = [(r, c + 1)] + ([(r + 1, c - 1), (r + 1, c)] if r % 2 == 0 else [(r + 1, c), (r + 1, c + 1)])
+        ext += [(i, idx[q]) for q in nb if q in idx]
+    left = [idx[(r, 0)] for r in range(nrow)]
+    right = [idx[(r, m if r % 2 == 0 else m - 1)] for r in range(nrow)]
+    w = [h * (0.5 if r in (0, nrow - 1) else 1.0) for r in range(nrow)]
+    return np.array(pts), ext, left, right, w
+
+
+def _cross_center_sheet(m):
+    """Unit square of m x m cells: cell edges plus a centre node joined to
+    the four corners."""
+    a = 1.0 / m
+    pts = [(i * a, j * a, 0.0) for j in range(m + 1) for i in range(m + 1)]
+    ext = []
+    for j in range(m + 1):
+        for i in range(m + 1):
+            if i < m:
+                ext.append((j * (m + 1) + i, j * (m + 1) + i + 1))
+            if j < m:
+                ext.append((j * (m + 1) + i, (j + 1) * (m + 1) + i))
+    for j in range(m):
+        for i in range(m):
+            c = len(pts)
+            pts.append(((i + 0.5) * a, (j + 0.5) * a, 0.0))
+            ext += [(c, jj * (m + 1) + ii) for ii, jj in ((i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1))]
+    left = [j * (m + 1) for j in range(m + 1)]
+    right = [j * (m + 1) + m for j in range(m + 1)]
+    w = [a * (0.5 if j in (0, m) else 1.0) for j in range(m + 1)]
+    return np.array(pts), ext, left, right, w
+
+
+def _k_over_Es(sheet, T=0.005):
+    """Sec. 2.4.2: uniaxial tension T per unit length on the left and right
+    edges of a sheet of unit springs (k = 1), E_s = T / strain; the static
+    state is reached by large damped BDF2 steps (no node is fixed: the
+    loads balance), as the paper reaches it by damped dynamics."""
+    x0, ext, left, right, w = sheet
+    ms = MassSpring(x0, 1.0, ext, 1.0)
+    fe = np.zeros_like(x0)
+    for l, r, wr in zip(left, right, w):
+        fe[l, 0] -= T * wr
+        fe[r, 0] += T * wr
+    for _ in range(40):
+        ms.step(100.0, fe, tol=1e-12, max_iter=50)
+    x, v = ms.state()
+    assert np.max(np.abs(v)) < 1e-12
+    strain = np.mean(x[right, 0] - x[left, 0]) / np.mean(x0[right, 0] - x0[left, 0]) - 1.0
+    return strain / T
+
+
+@pytest.mark.parametrize("mesh,m,target", [("triangle", 24, math.sqrt(3) / 2), ("cross", 16, 0.75)])
+def test_membrane_k_over_Es_converges_to_analytic(mesh, m, target):
+    """Sec. 2.4.2: with all stiffnesses k = 1 the ratio k/E_s of the sheet
+    converges under refinement to sqrt(3)/2 for the regular triangular mesh
+    and 3/4 for the cross-centre mesh (the printed analytic values). The
+    finite-sheet error is a boundary layer, O(1/m): doubling m halves it,
+    and the extrapolation 2 r(2m) - r(m) is within 0.5 % of the value."""
+    build = _tri_sheet if mesh == "triangle" else _cross_center_sheet
+    r1, r2 = _k_over_Es(build(m)), _k_over_Es(build(2 * m))
+    e1, e2 = abs(r1 / target - 1), abs(r2 / target - 1)
+    assert e2 < 0.6 * e1 and e2 < 0.05, (r1, r2)
+    assert abs((2 * r2 - r1) / target - 1) < 5e-3, (r1, r2)
