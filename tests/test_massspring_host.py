@@ -250,3 +250,36 @@ def test_membrane_k_over_Es_converges_to_analytic(mesh, m, target):
     e1, e2 = abs(r1 / target - 1), abs(r2 / target - 1)
     assert e2 < 0.6 * e1 and e2 < 0.05, (r1, r2)
     assert abs((2 * r2 - r1) / target - 1) < 5e-3, (r1, r2)
+
+
+def test_cantilever_free_vibration_converges_to_beam_mode():
+    """Sec. 2.4.1, dynamic case (length 1, mass per length 0.0571,
+    EI = 0.0259, the paper's 64 points): released from a small tip
+    deflection the network vibrates in its first mode; the period tends to
+    the Euler--Bernoulli 2 pi / (1.8751^2 sqrt(EI / (mu L^4))) as points are
+    added (errors about -1 %, -0.4 %, -0.04 % at 18, 34, 66 points)."""
+    L, EI, mu, dt = 1.0, 0.0259, 0.0571, 2e-3
+    want = 2 * math.pi / (1.8751040687 ** 2 * math.sqrt(EI / (mu * L ** 4)))
+    errs = []
+    for npts in (18, 34, 66):
+        seg = L / (npts - 1)
+        x0 = np.zeros((npts, 3))
+        x0[:, 0] = np.linspace(0.0, L, npts)
+        mass = np.full(npts, mu * seg)
+        mass[-1] = 0.5 * mu * seg
+        fixed = np.zeros(npts, bool)
+        fixed[:2] = True
+        ms = MassSpring(x0, mass, [(i, i + 1) for i in range(npts - 1)], 1e5,
+                        [(i, i + 1, i + 2) for i in range(npts - 2)], OM.kb_from_EI(EI, L, npts - 2), fixed=fixed)
+        fe = np.zeros((npts, 3))
+        fe[-1, 1] = -1e-5
+        ms.equilibrium(fe, load_steps=1, tol=1e-13)
+        ys = []
+        for _ in range(int(8.0 / dt)):
+            ms.step(dt, None, tol=1e-12)
+            ys.append(ms.state()[0][-1, 1])
+        ys = np.array(ys)
+        ts = dt * np.arange(1, len(ys) + 1)
+        up = [ts[i] - ys[i] * dt / (ys[i + 1] - ys[i]) for i in range(len(ys) - 1) if ys[i] < 0 <= ys[i + 1]]
+        errs.append(abs(np.mean(np.diff(up)) / want - 1))   # mean over the periods seen
+    assert errs[0] < 0.015 and errs[1] < 0.6 * errs[0] and errs[2] < 0.3 * errs[1] and errs[2] < 1e-3, errs

@@ -177,3 +177,38 @@ def test_moving_frame_free_particle_second_order():
     e = [_moving_frame_error(m) for m in (40, 80, 160)]
     assert e[2] < 2e-4, e
     assert 3.5 < e[0] / e[1] < 4.6 and 3.7 < e[1] / e[2] < 4.3, e
+
+
+def test_cantilever_free_vibration_period():
+    """Sec. 2.4.1, dynamic case (beam of length 1, mass per length 0.0571,
+    EI = 0.0259): released from a small tip deflection, the 10-point network
+    with lumped masses and k^b of Eq. (EI_k_relation) vibrates in its first
+    mode with the Euler--Bernoulli period 2 pi / (1.8751^2 sqrt(EI / (mu
+    L^4))) to within the 10-point discretisation error (-2.3 %; the host
+    solver's test shows the error vanishing with more points)."""
+    L, EI, mu, npts, dt = 1.0, 0.0259, 0.0571, 10, 0.02
+    seg = L / (npts - 1)
+    x0 = np.zeros((npts, 3))
+    x0[:, 0] = np.linspace(0.0, L, npts)
+    mass = np.full(npts, mu * seg)
+    mass[-1] = 0.5 * mu * seg
+    fixed = np.zeros(npts, bool)
+    fixed[:2] = True
+    net = M.Network(x0, mass, fixed, [(i, i + 1) for i in range(npts - 1)], np.full(npts - 1, 1e5),
+                    [(i, i + 1, i + 2) for i in range(npts - 2)], np.full(npts - 2, M.kb_from_EI(EI, L, npts - 2)))
+    fe = np.zeros((npts, 3))
+    fe[-1, 1] = -1e-5
+    x = M.equilibrium(net, fe, steps=1, tol=1e-13)
+    v = np.zeros_like(x)
+    xm1 = vm1 = None
+    ys = []
+    for _ in range(int(5.5 / dt)):
+        xn, vn, _ = M.bdf2_step(net, x, v, xm1, vm1, dt, dt, np.zeros_like(x), tol=1e-12)
+        xm1, vm1, x, v = x, v, xn, vn
+        ys.append(x[-1, 1])
+    ys = np.array(ys)
+    ts = dt * np.arange(1, len(ys) + 1)
+    up = [ts[i] - ys[i] * dt / (ys[i + 1] - ys[i]) for i in range(len(ys) - 1) if ys[i] < 0 <= ys[i + 1]]
+    period = up[1] - up[0]
+    want = 2 * math.pi / (1.8751040687 ** 2 * math.sqrt(EI / (mu * L ** 4)))
+    assert abs(period / want - 1) < 0.03, (period, want)
