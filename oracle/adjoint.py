@@ -45,7 +45,9 @@ def forward(p, u0, masks, weights, a, b):
 
 
 def adjoint(p, states, masks, weights, a, b):
-    """Reverse sweep. Returns per-step (dJ/dchi^n, dJ/dus^n) lists."""
+    """Reverse sweep (cubic boxes). Returns per-step (dJ/dchi^n, dJ/dus^n) lists."""
+    if p.nz != p.n:
+        raise ValueError("the adjoint oracle takes cubic boxes only")
     n = p.n
     n3 = float(n) ** 3
     keep = S.dealias_mask(n)

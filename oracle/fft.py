@@ -85,7 +85,8 @@ def rfft3(u):
 
 
 def irfft3(U, n):
-    """Inverse of ``rfft3``: rebuild the full Hermitian spectrum, transform back.
+    """Inverse of ``rfft3`` (n points along z; the x and y sizes are U's):
+    rebuild the full Hermitian spectrum, transform back.
 
     The missing kz = n/2+1..n-1 planes come from X(-k) = conj(X(k)); the
     result's imaginary part is dropped (it is zero up to rounding for a
@@ -94,10 +95,10 @@ def irfft3(U, n):
     U = np.asarray(U, dtype=np.complex128)
     full = np.zeros(U.shape[:-1] + (n,), dtype=np.complex128)
     full[..., : n // 2 + 1] = U
-    idx = np.arange(n)
-    neg = (-idx) % n
+    negx = (-np.arange(U.shape[-3])) % U.shape[-3]
+    negy = (-np.arange(U.shape[-2])) % U.shape[-2]
     for kz in range(n // 2 + 1, n):
         # X[kx, ky, kz] = conj(X[-kx, -ky, n-kz])
         src = U[..., :, :, n - kz]
-        full[..., :, :, kz] = np.conj(src[..., neg, :][..., :, neg])
+        full[..., :, :, kz] = np.conj(src[..., negx, :][..., :, negy])
     return ifftn3(full).real

@@ -104,14 +104,17 @@ def global_nodes(xw, frame):
     return np.asarray(frame["X_O"], dtype=np.float64)[None] + np.asarray(xw) @ R.T
 
 
-def rasterise(n, L, xw, vw, tri, frame, tw, h, profile=PROFILE_COS):
-    """chi [n,n,n] and u_s [3,n,n,n] (and the argmin triangle per point).
+def rasterise(n, L, xw, vw, tri, frame, tw, h, profile=PROFILE_COS, nz=None):
+    """chi [n,n,nz] and u_s [3,n,n,nz] (and the argmin triangle per point);
+    grid points (i, j, k) L/n, nz = n unless given.
 
     xw, vw: (n_nodes, 3) wing-frame positions and velocities; tri: (n_tri, 3)
     vertex indices; frame: dict with R (3x3 row-major, wing -> global), X_O,
     V_O, Omega.
     """
     dx = L / n
+    nz = n if nz is None else nz
+    dims = np.array([n, n, nz])
     R = np.asarray(frame["R"], dtype=np.float64).reshape(3, 3)
     XO = np.asarray(frame["X_O"], dtype=np.float64)
     VO = np.asarray(frame["V_O"], dtype=np.float64)
@@ -120,9 +123,9 @@ def rasterise(n, L, xw, vw, tri, frame, tw, h, profile=PROFILE_COS):
     vw = np.asarray(vw, dtype=np.float64)
     tri = np.asarray(tri, dtype=np.int64)
 
-    best = np.full((n, n, n), np.inf)
-    arg = np.full((n, n, n), -1, dtype=np.int64)
-    beta = np.zeros((n, n, n, 3))
+    best = np.full((n, n, nz), np.inf)
+    arg = np.full((n, n, nz), -1, dtype=np.int64)
+    beta = np.zeros((n, n, nz, 3))
     reach = tw + h
     for t_id in range(tri.shape[0]):
         A, B, C = xg[tri[t_id, 0]], xg[tri[t_id, 1]], xg[tri[t_id, 2]]
@@ -130,12 +133,12 @@ def rasterise(n, L, xw, vw, tri, frame, tw, h, profile=PROFILE_COS):
             lo = np.minimum(np.minimum(A, B), C) - reach
             hi = np.maximum(np.maximum(A, B), C) + reach
             i0 = np.maximum(np.ceil(lo / dx).astype(int), 0)
-            i1 = np.minimum(np.floor(hi / dx).astype(int), n - 1)
+            i1 = np.minimum(np.floor(hi / dx).astype(int), dims - 1)
             if np.any(i1 < i0):
                 continue
         else:
             i0 = np.array([0, 0, 0])
-            i1 = np.array([n - 1, n - 1, n - 1])
+            i1 = dims - 1
         gx = np.arange(i0[0], i1[0] + 1) * dx
         gy = np.arange(i0[1], i1[1] + 1) * dx
         gz = np.arange(i0[2], i1[2] + 1) * dx
@@ -160,7 +163,7 @@ def rasterise(n, L, xw, vw, tri, frame, tw, h, profile=PROFILE_COS):
     vloc = np.einsum("...v,...vc->...c", beta, vw[tv])
     vglob = vloc @ R.T
     X = np.arange(n) * dx
-    XX = np.stack(np.meshgrid(X, X, X, indexing="ij"), axis=-1)
+    XX = np.stack(np.meshgrid(X, X, np.arange(nz) * dx, indexing="ij"), axis=-1)
     r = XX - XO
     rot = np.cross(np.broadcast_to(Om, r.shape), r)
     us = VO + vglob + rot

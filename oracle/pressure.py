@@ -34,10 +34,10 @@ from . import step as S
 def total_pressure_hat(p, uh, chi, us):
     """Pi_hat (half spectrum, unnormalised DFT convention of ``oracle.step``)
     and the physical velocity of the state uh."""
-    keep = S.dealias_mask(p.n)
+    keep = S.dealias_mask(p.n, p.nz)
     wh = S.curl_hat(p, uh) * keep
-    u = S.to_physical(uh, p.n)
-    w = S.to_physical(wh, p.n)
+    u = S.to_physical(uh, p.nz)
+    w = S.to_physical(wh, p.nz)
     Nh = S.to_spectral(S.nonlinear_physical(u, w, chi, us, p.eta)) * keep
     kx, ky, kz = S.wavevectors(p)
     k2 = kx * kx + ky * ky + kz * kz
@@ -50,7 +50,7 @@ def total_pressure_hat(p, uh, chi, us):
 def static_pressure(p, uh, chi, us):
     """p = Pi - (1/2)|u|^2 on the grid."""
     Pih, u = total_pressure_hat(p, uh, chi, us)
-    return offt.irfft3(Pih, p.n) - 0.5 * np.sum(u * u, axis=0)
+    return offt.irfft3(Pih, p.nz) - 0.5 * np.sum(u * u, axis=0)
 
 
 def delta_cos4(r):
@@ -68,9 +68,10 @@ def delta_smoothed(r):
 
 
 def interpolate(pf, L, X):
-    """Delta interpolation of the grid field pf (n^3, periodic) at points X
-    (m, 3) with the smoothed kernel."""
+    """Delta interpolation of the grid field pf (n x n x nz, periodic, grid
+    spacing L/n on every axis) at points X (m, 3) with the smoothed kernel."""
     n = pf.shape[0]
+    dims = pf.shape
     dx = L / n
     X = np.asarray(X, dtype=np.float64)
     out = np.zeros(X.shape[0])
@@ -79,7 +80,7 @@ def interpolate(pf, L, X):
         lo = np.floor(g).astype(int) - 2
         idx = [np.arange(lo[a], lo[a] + 6) for a in range(3)]
         w = [delta_smoothed(g[a] - idx[a]) for a in range(3)]
-        sub = pf[np.ix_(idx[0] % n, idx[1] % n, idx[2] % n)]
+        sub = pf[np.ix_(idx[0] % dims[0], idx[1] % dims[1], idx[2] % dims[2])]
         out[m] = np.einsum("i,j,k,ijk->", w[0], w[1], w[2], sub)
     return out
 

@@ -6,8 +6,10 @@ Equation (Sec. 4.1, Eq. penalized Navier--Stokes, sponge term left out):
 
     d_t u + omega x u = -grad Pi + nu lap u - (chi / C_eta) (u - u_s),   div u = 0
 
-on the periodic box [0, L)^3 with n^3 points x_j = j dx, dx = L/n. With the
-total pressure eliminated by the Leray projection P, the spectral form is
+on the periodic box [0, L)^2 x [0, Lz) with n x n x nz points x_j = j dx,
+dx = L/n = Lz/nz (Lz = L, nz = n unless given: the paper's revolving-wing
+box of Sec. 4.2 is 4 x 4 x 2 with N x N x N/2 points). With the total
+pressure eliminated by the Leray projection P, the spectral form is
 
     d_t u_hat = -nu |k|^2 u_hat + P N_hat,
     N_hat     = F[ u x omega - (chi/eta)(u - u_s) ]   (omega x u moves to the
@@ -15,9 +17,10 @@ total pressure eliminated by the Leray projection P, the spectral form is
 
 Readings of points the paper leaves open:
 
-* Dealiasing: the cubic 2/3 rule -- a mode (m_x, m_y, m_z) is kept iff
-  3|m_i| < n on every axis (an integer test). It is applied to the initial
-  field, to omega_hat and to the whole N_hat (penalization included).
+* Dealiasing: the 2/3 rule on every axis -- a mode (m_x, m_y, m_z) is kept
+  iff 3|m_x| < n, 3|m_y| < n and 3|m_z| < nz (integer tests). It is applied
+  to the initial field, to omega_hat and to the whole N_hat (penalization
+  included).
 * Time scheme: the paper's "Adams--Bashforth" (Sec. 4.1, time-stepping
   paragraph) taken as fixed-step integrating-factor AB2 on v = e^{nu|k|^2 t} u_hat:
       u^{n+1} = E u^n + (dt/2) (3 E N^n - E^2 N^{n-1}),  E = exp(-nu |k|^2 dt),
@@ -57,6 +60,16 @@ class Params:
     dt: float
     x0: tuple = (0.0, 0.0, 0.0)
     mean_mode: int = MEAN_FIXED
+    nz: int = 0        # points along z (0: n)
+    Lz: float = 0.0    # box length along z (0: L nz / n, the same spacing)
+
+    def __post_init__(self):
+        if self.nz == 0:
+            self.nz = self.n
+        if self.Lz == 0.0:
+            self.Lz = self.L * self.nz / self.n
+        if abs(self.Lz / self.nz - self.L / self.n) > 1e-12 * self.L / self.n:
+            raise ValueError("the grid spacing must be the same on all axes")
 
 
 def mode_numbers(n):
@@ -66,23 +79,25 @@ def mode_numbers(n):
 
 
 def wavevectors(p):
-    """(kx, ky, kz) broadcastable over the half spectrum [kx][ky][kz<=n/2]."""
+    """(kx, ky, kz) broadcastable over the half spectrum [kx][ky][kz<=nz/2]."""
     n = p.n
     s = 2.0 * math.pi / p.L
     mx = mode_numbers(n)
-    mz = np.arange(n // 2 + 1)
+    mz = np.arange(p.nz // 2 + 1)
     kx = (s * mx)[:, None, None]
     ky = (s * mx)[None, :, None]
-    kz = (s * mz)[None, None, :]
+    kz = (2.0 * math.pi / p.Lz * mz)[None, None, :]
     return kx, ky, kz
 
 
-def dealias_mask(n):
-    """Boolean keep-mask of the 2/3 rule on the half spectrum."""
+def dealias_mask(n, nz=None):
+    """Boolean keep-mask of the 2/3 rule on the half spectrum (nz z points,
+    default n)."""
+    nz = n if nz is None else nz
     mx = np.abs(mode_numbers(n))
-    mz = np.arange(n // 2 + 1)
+    mz = np.arange(nz // 2 + 1)
     kx = 3 * mx < n
-    kz = 3 * mz < n
+    kz = 3 * mz < nz
     return kx[:, None, None] & kx[None, :, None] & kz[None, None, :]
 
 
@@ -132,7 +147,8 @@ def integrating_factor(p):
 def grid_coords(p):
     """Physical coordinates x_j = j dx of the three axes, broadcastable."""
     x = np.arange(p.n) * (p.L / p.n)
-    return x[:, None, None], x[None, :, None], x[None, None, :]
+    z = np.arange(p.nz) * (p.Lz / p.nz)
+    return x[:, None, None], x[None, :, None], z[None, None, :]
 
 
 def to_spectral(u):
@@ -140,9 +156,10 @@ def to_spectral(u):
     return np.stack([offt.rfft3(c) for c in u])
 
 
-def to_physical(uh, n):
-    """Inverse transform of the three components of a half spectrum."""
-    return np.stack([offt.irfft3(c, n) for c in uh])
+def to_physical(uh, nz):
+    """Inverse transform of the three components of a half spectrum (nz
+    points along z)."""
+    return np.stack([offt.irfft3(c, nz) for c in uh])
 
 
 def nonlinear_physical(u, w, chi, us, eta):
@@ -158,10 +175,10 @@ def penalization_force(p, u, chi, us):
     dx3 = (p.L / p.n) ** 3
     pen = chi[None] * (u - us)
     X, Y, Z = grid_coords(p)
-    n = p.n
-    rx = np.broadcast_to(X - p.x0[0], (n, n, n))
-    ry = np.broadcast_to(Y - p.x0[1], (n, n, n))
-    rz = np.broadcast_to(Z - p.x0[2], (n, n, n))
+    shape = (p.n, p.n, p.nz)
+    rx = np.broadcast_to(X - p.x0[0], shape)
+    ry = np.broadcast_to(Y - p.x0[1], shape)
+    rz = np.broadcast_to(Z - p.x0[2], shape)
     mom = [ry * pen[2] - rz * pen[1],
            rz * pen[0] - rx * pen[2],
            rx * pen[1] - ry * pen[0]]
@@ -175,14 +192,14 @@ class Solver:
 
     def __init__(self, p):
         self.p = p
-        n = p.n
-        self.keep = dealias_mask(n)
+        n, nz = p.n, p.nz
+        self.keep = dealias_mask(n, nz)
         self.E = integrating_factor(p)
-        self.uh = np.zeros((3, n, n, n // 2 + 1), dtype=np.complex128)
+        self.uh = np.zeros((3, n, n, nz // 2 + 1), dtype=np.complex128)
         self.Nprev = np.zeros_like(self.uh)
         self.nstep = 0
-        self.chi = np.zeros((n, n, n))
-        self.us = np.zeros((3, n, n, n))
+        self.chi = np.zeros((n, n, nz))
+        self.us = np.zeros((3, n, n, nz))
         self.F = np.zeros(3)
         self.M = np.zeros(3)
         self.chi_sp = None
@@ -214,14 +231,14 @@ class Solver:
         self.c_sp = float(c_sp)
 
     def velocity(self):
-        return to_physical(self.uh, self.p.n)
+        return to_physical(self.uh, self.p.nz)
 
     def rhs_hat(self):
         """Projected, truncated N_hat of the current state; sets F, M."""
         p = self.p
         wh = curl_hat(p, self.uh) * self.keep
-        u = to_physical(self.uh, p.n)
-        w = to_physical(wh, p.n)
+        u = to_physical(self.uh, p.nz)
+        w = to_physical(wh, p.nz)
         self.F, self.M = penalization_force(p, u, self.chi, self.us)
         nl = nonlinear_physical(u, w, self.chi, self.us, p.eta)
         Nh = to_spectral(nl) * self.keep
@@ -244,17 +261,17 @@ class Solver:
 
     def energy(self):
         """(1/2) integral |u|^2 dV via Parseval on the half spectrum."""
-        n = self.p.n
-        w = np.full(n // 2 + 1, 2.0)
+        n, nz = self.p.n, self.p.nz
+        w = np.full(nz // 2 + 1, 2.0)
         w[0] = 1.0
-        if n % 2 == 0:
-            w[n // 2] = 1.0
+        if nz % 2 == 0:
+            w[nz // 2] = 1.0
         s = np.sum(np.abs(self.uh) ** 2 * w[None, None, None, :])
-        return 0.5 * s * self.p.L ** 3 / float(n) ** 6
+        return 0.5 * s * self.p.L ** 2 * self.p.Lz / (float(n) ** 2 * nz) ** 2
 
     def max_divergence(self):
         """max |k . c_k| over the half spectrum, c_k = DFT(u)_k / n^3 the
         Fourier coefficients (so the value does not scale with n)."""
         kx, ky, kz = wavevectors(self.p)
         d = kx * self.uh[0] + ky * self.uh[1] + kz * self.uh[2]
-        return float(np.max(np.abs(d))) / float(self.p.n) ** 3
+        return float(np.max(np.abs(d))) / (float(self.p.n) ** 2 * self.p.nz)
