@@ -283,3 +283,22 @@ def test_cantilever_free_vibration_converges_to_beam_mode():
         up = [ts[i] - ys[i] * dt / (ys[i + 1] - ys[i]) for i in range(len(ys) - 1) if ys[i] < 0 <= ys[i + 1]]
         errs.append(abs(np.mean(np.diff(up)) / want - 1))   # mean over the periods seen
     assert errs[0] < 0.015 and errs[1] < 0.6 * errs[0] and errs[2] < 0.3 * errs[1] and errs[2] < 1e-3, errs
+
+
+def test_degenerate_networks():
+    """All nodes fixed: a step and an equilibrium leave the state alone; a
+    zero load keeps the rest state; a free node with no springs moves on a
+    straight line (BDF2 is exact for it)."""
+    x0 = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0], [0.2, 0.01, 0.0]])
+    ms = MassSpring(x0, 1.0, [(0, 1), (1, 2)], 10.0, [(0, 1, 2)], 0.1, fixed=[True, True, True])
+    assert ms.info()[0] == 0
+    assert ms.step(0.01, np.ones((3, 3))) >= 1
+    x, v = ms.state()
+    assert np.all(x == x0) and np.all(v == 0)
+    ms2 = MassSpring(x0, 1.0, [(0, 1), (1, 2)], 10.0, [(0, 1, 2)], 0.1, fixed=[True, True, False])
+    ms2.equilibrium(np.zeros((3, 3)), load_steps=2)
+    assert np.max(np.abs(ms2.state()[0] - x0)) < 1e-14
+    free = MassSpring(np.array([[0.5, 0.5, 0.5]]), 2.0, np.zeros((0, 2), int), [], v0=np.array([[0.1, -0.2, 0.3]]))
+    for dt in (0.1, 0.2, 0.05):
+        free.step(dt)
+    assert np.allclose(free.state()[0], [[0.5 + 0.035, 0.5 - 0.07, 0.5 + 0.105]], atol=1e-14)
