@@ -24,6 +24,10 @@
  * - Work is enqueued on the CUDA stream given to ps_init and is
  *   asynchronous unless a call says it synchronises. Asynchronous CUDA
  *   errors surface as PS_ECUDA at the next synchronising call.
+ * - Fault injection for tests: with the environment variable
+ *   PS_FAULT_ALLOC set to "ctx" (ps_init), "ms" (ps_ms_create) or "all",
+ *   those calls fail their host allocation and return PS_ENOMEM (before
+ *   any CUDA call).
  */
 #ifndef PS_H
 #define PS_H
@@ -359,6 +363,18 @@ ps_status ps_ms_step(ps_ms* m, double dt, const double* f_ext, const ps_ms_frame
  * PS_ENUMERIC (state unchanged) if a load increment does not converge. */
 ps_status ps_ms_equilibrium(ps_ms* m, const double* f_ext, int32_t load_steps, double tol, int32_t max_iter,
                             int32_t* iters_out);
+
+/* Checkpoint of the network's time-stepping state (positions, velocities,
+ * the previous level of both and the previous step, for the BDF2 history)
+ * to/from a caller host buffer of ps_ms_state_size() bytes. Saving makes
+ * the next step rebuild its Newton matrix, as a restored network does, so a
+ * run continued after ps_ms_save and one resumed by ps_ms_restore give the
+ * same bits. ps_ms_restore returns PS_EINVAL for a buffer that is not a
+ * state of a network with this node count (springs are not stored: restore
+ * into a network built from the same inputs). */
+ps_status ps_ms_state_size(const ps_ms* m, size_t* bytes);
+ps_status ps_ms_save(ps_ms* m, void* buf);
+ps_status ps_ms_restore(ps_ms* m, const void* buf);
 
 /* Text of the last error on this network ("" if none). */
 const char* ps_ms_last_error(const ps_ms* m);

@@ -84,6 +84,9 @@ _SIGS = {
     "ps_ms_step": (c_int32, [c_void_p, c_double, c_void_p, _P(PsMsFrame), c_double, c_int32, _P(c_int32)]),
     "ps_ms_equilibrium": (c_int32, [c_void_p, c_void_p, c_int32, c_double, c_int32, _P(c_int32)]),
     "ps_ms_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ps_ms_state_size": (c_int32, [c_void_p, _P(c_size_t)]),
+    "ps_ms_save": (c_int32, [c_void_p, c_void_p]),
+    "ps_ms_restore": (c_int32, [c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -337,3 +340,17 @@ def make_ms_frame(A_O=(0.0, 0.0, 0.0), Omega=(0.0, 0.0, 0.0), dOmega=(0.0, 0.0, 
     for i in range(3):
         f.A_O[i], f.Omega[i], f.dOmega[i] = float(A_O[i]), float(Omega[i]), float(dOmega[i])
     return f
+
+
+def ps_ms_save(m):
+    """The network's state as bytes."""
+    nb = c_size_t(0)
+    ms_check(lib().ps_ms_state_size(m, ctypes.byref(nb)), m)
+    buf = ctypes.create_string_buffer(nb.value)
+    ms_check(lib().ps_ms_save(m, buf), m)
+    return buf.raw
+
+
+def ps_ms_restore(m, data):
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    ms_check(lib().ps_ms_restore(m, buf), m)

@@ -13,6 +13,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "ps_fault.h"
 #include "ps.h"
 #include "ps_engine.cuh"
 #include "ps_mask.cuh"
@@ -471,7 +472,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     layout_for(p, ops, &L);
     if (workspace_bytes < L.total) return PS_ENOMEM;
 
-    ps_ctx* c = new (std::nothrow) ps_ctx();
+    ps_ctx* c = ps_fault_alloc("ctx") ? nullptr : new (std::nothrow) ps_ctx();
     if (!c) return PS_ENOMEM;
     c->p = *p;
     c->stream = (cudaStream_t)cuda_stream;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "ps.h"
+#include "ps_fault.h"
 
 namespace {
 
@@ -299,7 +300,7 @@ ps_status ps_ms_create(int32_t n_nodes, const double* mass, const double* x0, co
         if (i < 0 || i >= n_nodes || j < 0 || j >= n_nodes || k < 0 || k >= n_nodes || i == j || j == k || i == k)
             return PS_EINVAL;
     }
-    ps_ms* m = new (std::nothrow) ps_ms();
+    ps_ms* m = ps_fault_alloc("ms") ? nullptr : new (std::nothrow) ps_ms();
     if (!m) return PS_ENOMEM;
     m->n = n_nodes;
     m->x.assign(x0, x0 + 3 * n_nodes);
@@ -563,6 +564,55 @@ ps_status ps_ms_equilibrium(ps_ms* m, const double* f_ext, int32_t load_steps, d
     m->steps = 0;
     m->j_valid = false;
     if (iters_out) *iters_out = total;
+    return PS_OK;
+}
+
+// Checkpoint layout: 8-byte tag, node count, step count (int64), previous
+// step (double), then x, v, x^{n-1}, v^{n-1} (3n doubles each).
+static const char kMsTag[8] = {'p', 's', 'm', 's', 'v', '0', '0', '1'};
+
+ps_status ps_ms_state_size(const ps_ms* m, size_t* bytes) {
+    if (!m || !bytes) return PS_EINVAL;
+    *bytes = 32 + 4 * sizeof(double) * 3 * (size_t)m->n;
+    return PS_OK;
+}
+
+ps_status ps_ms_save(ps_ms* m, void* buf) {
+    if (!m || !buf) return PS_EINVAL;
+    unsigned char* d = (unsigned char*)buf;
+    const int64_t hdr[2] = {m->n, m->steps};
+    memcpy(d, kMsTag, 8);
+    memcpy(d + 8, hdr, 16);
+    memcpy(d + 24, &m->dt_prev, 8);
+    const size_t b = sizeof(double) * 3 * (size_t)m->n;
+    memcpy(d + 32, m->x.data(), b);
+    memcpy(d + 32 + b, m->v.data(), b);
+    const bool hist = m->steps > 0;
+    memcpy(d + 32 + 2 * b, (hist ? m->xm1 : m->x).data(), b);
+    memcpy(d + 32 + 3 * b, (hist ? m->vm1 : m->v).data(), b);
+    // the next step rebuilds its Newton matrix, as a restored network does
+    m->j_valid = false;
+    return PS_OK;
+}
+
+ps_status ps_ms_restore(ps_ms* m, const void* buf) {
+    if (!m || !buf) return PS_EINVAL;
+    const unsigned char* d = (const unsigned char*)buf;
+    int64_t hdr[2];
+    memcpy(hdr, d + 8, 16);
+    if (memcmp(d, kMsTag, 8) != 0 || hdr[0] != m->n || hdr[1] < 0) {
+        m->err = "ps_ms_restore: not a state of a network with this node count";
+        return PS_EINVAL;
+    }
+    const double* q = (const double*)(d + 32);
+    const size_t n3 = 3 * (size_t)m->n;
+    memcpy(&m->dt_prev, d + 24, 8);
+    m->steps = (long)hdr[1];
+    m->x.assign(q, q + n3);
+    m->v.assign(q + n3, q + 2 * n3);
+    m->xm1.assign(q + 2 * n3, q + 3 * n3);
+    m->vm1.assign(q + 3 * n3, q + 4 * n3);
+    m->j_valid = false;
     return PS_OK;
 }
 

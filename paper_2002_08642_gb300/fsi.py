@@ -78,3 +78,30 @@ class FSI:
     def state(self):
         """Wing-frame node positions and velocities (host)."""
         return self.ms.state()
+
+    def save(self, path):
+        """Checkpoint of the coupled state to a host file: the fluid's
+        time-stepping state, the network's (with its BDF2 history) and the
+        time. The mask is not stored: ``load`` rasterises it again from the
+        restored nodes."""
+        buf = self.solver.state_buffer()
+        self.solver.save_state(buf)
+        ms = np.frombuffer(self.ms.save(), dtype=np.uint8)
+        np.savez(path, fluid=buf.cpu().numpy(), ms=ms, t=self.t, dt=self.dt)
+
+    def load(self, path):
+        """Resume from ``save`` (same solver parameters and network inputs):
+        the coupled steps that follow give the same results as the run that
+        was saved."""
+        with np.load(path) as f:
+            if float(f["dt"]) != self.dt:
+                raise ValueError("checkpoint dt %s, coupling has %s" % (float(f["dt"]), self.dt))
+            fluid = torch.from_numpy(np.ascontiguousarray(f["fluid"]))
+            ms = f["ms"].tobytes()
+            t = float(f["t"])
+        buf = self.solver.state_buffer()
+        buf.copy_(fluid)
+        self.solver.restore_state(buf)
+        self.ms.restore(ms)
+        self.t = t
+        self._upload_and_mask()

@@ -71,6 +71,14 @@ class MassSpring:
         v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
         B.ps_ms_set_state(self._m, _ptr(x), _ptr(v))
 
+    def save(self):
+        """Time-stepping state (with the BDF2 history) as bytes."""
+        return B.ps_ms_save(self._m)
+
+    def restore(self, data):
+        """Restore a state from ``save`` of a network built from the same inputs."""
+        B.ps_ms_restore(self._m, data)
+
     def step(self, dt, f_ext=None, frame=None, tol=1e-10, max_iter=30):
         """One BDF2 step; frame = dict(A_O, Omega, dOmega) in the network's
         axes, or None for an inertial frame. Returns Newton iterations."""

@@ -4,6 +4,7 @@ C ABI; nothing is computed here.
 """
 import math
 
+import numpy as np
 import torch
 
 from . import binding as B
@@ -174,3 +175,27 @@ class Solver:
 
     def restore_state(self, buf):
         B.ps_restore_state(self.ctx, buf.data_ptr())
+
+    def save_checkpoint(self, path):
+        """Write the time-stepping state (spectral velocity, AB2 history,
+        step counter) and the parameters it belongs to to a host file."""
+        buf = self.state_buffer()
+        self.save_state(buf)
+        p = self.params
+        np.savez(path, state=buf.cpu().numpy(), n=p.n, precision=p.precision, L=p.L, nu=p.nu, eta=p.eta,
+                 dt=p.dt)
+
+    def load_checkpoint(self, path):
+        """Restore a state written by ``save_checkpoint`` of a solver with the
+        same grid, precision and parameters (ValueError otherwise)."""
+        with np.load(path) as f:
+            p = self.params
+            for k in ("n", "precision", "L", "nu", "eta", "dt"):
+                if float(f[k]) != float(getattr(p, k)):
+                    raise ValueError("checkpoint %s = %s, solver has %s" % (k, f[k], getattr(p, k)))
+            state = torch.from_numpy(np.ascontiguousarray(f["state"]))
+        buf = self.state_buffer()
+        if state.numel() != buf.numel():
+            raise ValueError("checkpoint state size does not match")
+        buf.copy_(state)
+        self.restore_state(buf)

@@ -45,6 +45,24 @@ class OracleFluid:
         self.calls.append("pressure")
         return torch.from_numpy(OP.static_pressure(self.p, self.fluid.uh, self.fluid.chi, self.fluid.us))
 
+    def state_buffer(self):
+        return torch.empty(2 * self.fluid.uh.nbytes + 8, dtype=torch.uint8)
+
+    def save_state(self, buf):
+        b = buf.numpy()
+        nb = self.fluid.uh.nbytes
+        b[:nb] = np.frombuffer(self.fluid.uh.tobytes(), dtype=np.uint8)
+        b[nb:2 * nb] = np.frombuffer(self.fluid.Nprev.tobytes(), dtype=np.uint8)
+        b[2 * nb:] = np.frombuffer(np.int64(self.fluid.nstep).tobytes(), dtype=np.uint8)
+
+    def restore_state(self, buf):
+        b = buf.numpy()
+        nb = self.fluid.uh.nbytes
+        shape = self.fluid.uh.shape
+        self.fluid.uh = np.frombuffer(b[:nb].tobytes(), dtype=np.complex128).reshape(shape).copy()
+        self.fluid.Nprev = np.frombuffer(b[nb:2 * nb].tobytes(), dtype=np.complex128).reshape(shape).copy()
+        self.fluid.nstep = int(np.frombuffer(b[2 * nb:].tobytes(), dtype=np.int64)[0])
+
     def pressure_loads(self, pf, xw, tri, frame):
         self.calls.append("loads")
         xg = OM.global_nodes(xw.numpy(), frame)
@@ -76,3 +94,37 @@ def test_coupling_order_frames_and_load_rotation():
     assert np.max(np.abs(x - o.x)) < 1e-8 * np.max(np.abs(o.x - w["x0"])) + 1e-14
     assert np.max(np.abs(v - o.v)) < 1e-6 * np.max(np.abs(o.v))
     assert abs(c.t - 2 * dt) < 1e-15
+
+
+def test_coupled_checkpoint_resume(tmp_path):
+    """FSI.save / FSI.load: a coupled run resumed from a checkpoint file
+    (fluid state, network state with its BDF2 history, time; the mask
+    rasterised again from the restored nodes) continues with the same
+    results as the run that was saved."""
+    pbuild.build()
+    n, L, nu, eta, dt = 16, 4.0, 1.527e-4, 1e-2, 2e-3
+    w = inputs.fsi_wing(ns=4, nc=2, veins=(0, 2), kb=0.05, ke=20.0, mass=0.05)
+
+    def frames(t):
+        return inputs.revolving_frames(t, tau=0.05)
+
+    u0 = inputs.random_field(n, L, seed=6, rms=0.3)
+    p = S.Params(n=n, L=L, nu=nu, eta=eta, dt=dt, x0=(2.0, 2.0, 2.0))
+    tw, h = 2 * L / n, 1.5 * L / n
+
+    def make():
+        ms = MassSpring(w["x0"], w["mass"], w["ext"], w["ke"], w["bend"], w["kb"], fixed=w["fixed"])
+        fake = OracleFluid(p, u0, tw, h)
+        return fake, FSI(fake, ms, w["tri"], frames, tol=1e-12)
+
+    fa, a = make()
+    a.step(1)
+    a.save(tmp_path / "fsi.npz")
+    a.step(2)
+    fb, b = make()
+    b.load(tmp_path / "fsi.npz")
+    b.step(2)
+    xa, va = a.state()
+    xb, vb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(fa.fluid.uh, fb.fluid.uh) and b.t == a.t

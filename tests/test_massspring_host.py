@@ -302,3 +302,53 @@ def test_degenerate_networks():
     for dt in (0.1, 0.2, 0.05):
         free.step(dt)
     assert np.allclose(free.state()[0], [[0.5 + 0.035, 0.5 - 0.07, 0.5 + 0.105]], atol=1e-14)
+
+
+def test_checkpoint_resume_is_bitwise():
+    """ps_ms_save / ps_ms_restore carry the BDF2 history: a run continued
+    after a save and a fresh network restored from it take the same steps
+    to the same bits (saving also rebuilds the Newton matrix)."""
+    x0, mass, fixed, ext, ke, bend, kb = random_network(seed=21)
+    fe = np.zeros_like(x0)
+    fe[-1] = (0.2, -0.4, 0.3)
+    fr = dict(A_O=(0.0, 0.1, 0.0), Omega=(0.0, 0.2, 1.0), dOmega=(0.0, 0.0, 0.3))
+    a = MassSpring(x0, mass, ext, ke, bend, kb, fixed=fixed)
+    for dt in (0.02, 0.03):
+        a.step(dt, fe, frame=fr)
+    blob = a.save()
+    for dt in (0.025, 0.02, 0.02):
+        a.step(dt, fe, frame=fr)
+    b = MassSpring(x0, mass, ext, ke, bend, kb, fixed=fixed)
+    b.restore(blob)
+    for dt in (0.025, 0.02, 0.02):
+        b.step(dt, fe, frame=fr)
+    xa, va = a.state()
+    xb, vb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    c = MassSpring(x0[:5], mass[:5], [(0, 1)], 1.0)
+    with pytest.raises(B.PsError):
+        c.restore(blob)
+
+
+def test_fault_injection_on_the_host(monkeypatch):
+    """PS_FAULT_ALLOC makes ps_ms_create and ps_init fail their host
+    allocation with PS_ENOMEM (ps_init before any CUDA call)."""
+    import ctypes
+
+    from paper_2002_08642_gb300.solver import make_params
+
+    x0 = np.zeros((3, 3))
+    x0[:, 0] = (0.0, 1.0, 2.0)
+    monkeypatch.setenv("PS_FAULT_ALLOC", "ms")
+    with pytest.raises(B.PsError) as e:
+        MassSpring(x0, 1.0, [(0, 1), (1, 2)], 1.0)
+    assert e.value.status == B.PS_ENOMEM
+    p = make_params(32, 4.0, 0.01, 1.0, 1e-3)
+    need = B.ps_workspace_size(p)
+    for what, expect in (("ctx", B.PS_ENOMEM), ("all", B.PS_ENOMEM)):
+        monkeypatch.setenv("PS_FAULT_ALLOC", what)
+        ctx = ctypes.c_void_p(0)
+        st = B.lib().ps_init(ctypes.byref(p), None, ctypes.c_void_p(1 << 20), need, ctypes.byref(ctx))
+        assert st == expect and not ctx.value
+    monkeypatch.setenv("PS_FAULT_ALLOC", "ctx")
+    assert MassSpring(x0, 1.0, [(0, 1), (1, 2)], 1.0).info()[0] == 3
