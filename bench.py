@@ -230,6 +230,7 @@ def run_ours(args, cfg):
 
     from paper_2002_08642_gb300 import build as pbuild
     from paper_2002_08642_gb300 import inputs
+    from paper_2002_08642_gb300.forces import lift_drag
     from paper_2002_08642_gb300.solver import Solver
 
     rank = int(os.environ.get("RANK", "0"))
@@ -349,7 +350,7 @@ def run_ours(args, cfg):
         "passes_ms": {k: v[0] / max(v[1], 1) for k, v in passes.items()},
         "e2e": {"value": e2e, "unit": "Mpts*steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": kernels_per_step * args.steps,
-        "forces_last": {"F": F, "M": M},
+        "forces_last": {"F": F, "M": M, "lift_drag": lift_drag(F, frames[total - 1]["R"])},
     }
     if clk:
         out["clocks"] = clk
