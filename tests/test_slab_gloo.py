@@ -2,8 +2,10 @@
 processes with gloo: the two exchanges against the global arrays, and a
 distributed 3-D forward transform (z and y on x-slabs, exchange, x on
 ky-slabs) against the oracle's transform with the 2/3 truncation."""
+import datetime
 import os
 import socket
+import traceback
 
 import numpy as np
 import pytest
@@ -24,9 +26,16 @@ def _port():
 
 
 def _worker(rank, world, port, n, q):
+    try:
+        _work(rank, world, port, n, q)
+    except Exception:
+        q.put((rank, False, False, False, traceback.format_exc()))
+
+
+def _work(rank, world, port, n, q):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
     try:
         mm = (n - 1) // 3
         K, Kz = 2 * mm + 1, mm + 1
@@ -63,15 +72,18 @@ def _worker(rank, world, port, n, q):
 @pytest.mark.parametrize("world,n", [(2, 12), (3, 16)])
 def test_slab_exchanges_and_distributed_transform(world, n):
     ctx = mp.get_context("spawn")
-    q = ctx.SimpleQueue()
+    q = ctx.Queue()
     port = _port()
     procs = [ctx.Process(target=_worker, args=(r, world, port, n, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = [q.get() for _ in range(world)]
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
+    try:
+        res = [q.get(timeout=120) for _ in range(world)]
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
     for r, ok1, ok2, ok3, ok4 in res:
         assert ok1 and ok2 and ok3 and ok4, (r, ok1, ok2, ok3, ok4)
 
