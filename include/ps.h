@@ -211,7 +211,10 @@ ps_status ps_pressure_loads(ps_ctx* ctx, const void* p_dev, const double* xw_dev
 ps_status ps_diagnostics(ps_ctx* ctx, double* energy, double* max_div);
 
 /* Checkpoint of the time-stepping state (spectral velocity, AB2 history,
- * step counter) to/from caller device memory of ps_state_size() bytes. */
+ * step counter) to/from caller device memory of ps_state_size() bytes,
+ * 16-byte aligned (PS_EINVAL for a null or unaligned buffer). Both calls
+ * synchronise the stream. The mask and the sponge are not part of the state;
+ * after a restore the next step runs all passes (keep_uw). */
 ps_status ps_state_size(const ps_ctx* ctx, size_t* bytes);
 ps_status ps_save_state(ps_ctx* ctx, void* buf_dev);
 ps_status ps_restore_state(ps_ctx* ctx, const void* buf_dev);
