@@ -10,8 +10,9 @@ order, for the objective
 n). Inner products: physical arrays sum_j x_j y_j; half-spectrum arrays
 Re sum w_kz conj(x) y with w = 1 on the kz = 0 plane and 2 elsewhere, which is
 the full-spectrum sum for Hermitian data. With the oracle's transforms
-(rfft3 = DFT, irfft3 = inverse DFT with 1/n^3) the adjoints are
-    rfft3*  = n^3 irfft3,   irfft3* = rfft3 / n^3,
+(rfft3 = DFT, irfft3 = inverse DFT with 1/N, N = n n nz the grid points)
+the adjoints are
+    rfft3*  = N irfft3,   irfft3* = rfft3 / N,
 and truncation, projection, integrating factor and i k x are self-adjoint
 mode by mode.
 
@@ -45,25 +46,24 @@ def forward(p, u0, masks, weights, a, b):
 
 
 def adjoint(p, states, masks, weights, a, b):
-    """Reverse sweep (cubic boxes). Returns per-step (dJ/dchi^n, dJ/dus^n) lists."""
-    if p.nz != p.n:
-        raise ValueError("the adjoint oracle takes cubic boxes only")
-    n = p.n
-    n3 = float(n) ** 3
-    keep = S.dealias_mask(n)
+    """Reverse sweep. Returns per-step (dJ/dchi^n, dJ/dus^n) lists."""
+    n, nz = p.n, p.nz
+    n3 = float(n) * n * nz          # points of the grid: rfft3* = n3 irfft3
+    keep = S.dealias_mask(n, nz)
     E = S.integrating_factor(p)
     dt = p.dt
     dx3 = (p.L / n) ** 3
     X, Y, Z = S.grid_coords(p)
-    r = [np.broadcast_to(X - p.x0[0], (n, n, n)), np.broadcast_to(Y - p.x0[1], (n, n, n)),
-         np.broadcast_to(Z - p.x0[2], (n, n, n))]
+    shape = (n, n, nz)
+    r = [np.broadcast_to(X - p.x0[0], shape), np.broadcast_to(Y - p.x0[1], shape),
+         np.broadcast_to(Z - p.x0[2], shape)]
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     # dJ/dp_j = a + b x r_j  (p = chi (u - us))
     bxr = np.stack([b[1] * r[2] - b[2] * r[1], b[2] * r[0] - b[0] * r[2], b[0] * r[1] - b[1] * r[0]])
     gp = a[:, None, None, None] + bxr
 
-    lam = np.zeros((3, n, n, n // 2 + 1), dtype=np.complex128)
+    lam = np.zeros((3, n, n, nz // 2 + 1), dtype=np.complex128)
     mu = np.zeros_like(lam)
     K = len(states)
     gchi = [None] * K
@@ -78,10 +78,10 @@ def adjoint(p, states, masks, weights, a, b):
         lam_new = E * lam
         mu_new = -(0.5 * dt * E * E) * lam if k > 0 else np.zeros_like(lam)
         # G = P keep rfft3(nl)  ->  nl_bar = n^3 irfft3(keep P Gbar)
-        nlb = n3 * S.to_physical(S.project(p, Gbar) * keep, n)
+        nlb = n3 * S.to_physical(S.project(p, Gbar) * keep, nz)
         # recompute the forward quantities of step k
-        u = S.to_physical(uh, n)
-        w = S.to_physical(S.curl_hat(p, uh) * keep, n)
+        u = S.to_physical(uh, nz)
+        w = S.to_physical(S.curl_hat(p, uh) * keep, nz)
         # nl = u x w - c (u - us)
         ub = np.stack([w[1] * nlb[2] - w[2] * nlb[1],
                        w[2] * nlb[0] - w[0] * nlb[2],

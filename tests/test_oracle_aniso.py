@@ -148,3 +148,38 @@ def test_mask_and_interpolation_on_the_anisotropic_grid():
     b = OP.interpolate(pf, L, pts + np.array([L, 0.0, nz * dx]))
     assert np.allclose(a, b, atol=1e-13)
     assert np.allclose(OP.interpolate(np.ones((n, n, nz)), L, pts), 1.0, atol=1e-14)
+
+
+def test_adjoint_on_the_anisotropic_box_matches_central_differences():
+    """The oracle adjoint on the N x N x N/2 grid (rfft3* = N irfft3 with
+    N = n^2 nz points): dJ/dchi and dJ/du_s against central differences of
+    the oracle forward over three masked steps."""
+    from oracle import adjoint as OA
+
+    n, nz, K = 16, 8, 3
+    p = S.Params(n=n, L=4.0, nu=0.02, eta=0.05, dt=2e-3, x0=(1.9, 2.1, 1.05), nz=nz)
+    rng = np.random.default_rng(2)
+    X, Y, Z = grid(p)
+    u0 = np.stack([np.sin(np.pi * Y / 2) * np.cos(np.pi * Z), np.sin(np.pi * Z) * np.cos(np.pi * X / 2),
+                   0.3 * np.cos(np.pi * (X + Y) / 2)])
+    masks = []
+    for _ in range(K):
+        chi = np.zeros((n, n, nz))
+        chi[4:10, 5:11, 2:6] = rng.uniform(0.2, 1.0, (6, 6, 4))
+        masks.append((chi, rng.standard_normal((3, n, n, nz)) * 0.1))
+    w = np.full(K, 1.0 / K)
+    a, b = np.array([0.3, -0.2, 1.0]), np.array([0.1, 0.4, -0.3])
+    J, states = OA.forward(p, u0, masks, w, a, b)
+    gchi, gus = OA.adjoint(p, states, masks, w, a, b)
+    h = 1e-5
+    for k in (0, 2):
+        dchi = np.zeros((n, n, nz))
+        dchi[4:10, 5:11, 2:6] = rng.uniform(-1, 1, (6, 6, 4))
+        dus = rng.standard_normal((3, n, n, nz))
+        for which, d, g in ((0, dchi, gchi[k]), (1, dus, gus[k])):
+            def shifted(s):
+                return [m if i != k else ((m[0] + s * d, m[1]) if which == 0 else (m[0], m[1] + s * d))
+                        for i, m in enumerate(masks)]
+            fd = (OA.forward(p, u0, shifted(h), w, a, b)[0] - OA.forward(p, u0, shifted(-h), w, a, b)[0]) / (2 * h)
+            ad = float(np.sum(g * d))
+            assert abs(fd - ad) < 1e-7 * max(abs(fd), 1e-12), (k, which, fd, ad)
