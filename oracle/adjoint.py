@@ -115,10 +115,11 @@ def _prof_deriv(delta, tw, h, profile):
     return np.where(ramp, -0.5 * math.pi / (2.0 * h) * np.sin(math.pi * (delta - tw + h) / (2.0 * h)), 0.0)
 
 
-def rasterise_vjp(n, L, xw, vw, tri, frame, tw, h, chi_bar, us_bar, profile=OM.PROFILE_COS):
-    """dJ/dxw (n_nodes x 3, wing frame) given dJ/dchi, dJ/dus on the grid,
-    for the mask of ``oracle.mask.rasterise`` with its argmin held fixed."""
-    chi, us, arg, best = OM.rasterise(n, L, xw, vw, tri, frame, tw, h, profile)
+def rasterise_vjp(n, L, xw, vw, tri, frame, tw, h, chi_bar, us_bar, profile=OM.PROFILE_COS, nz=None):
+    """dJ/dxw (n_nodes x 3, wing frame) given dJ/dchi, dJ/dus on the grid
+    (n x n x nz, nz = n unless given), for the mask of
+    ``oracle.mask.rasterise`` with its argmin held fixed."""
+    chi, us, arg, best = OM.rasterise(n, L, xw, vw, tri, frame, tw, h, profile, nz=nz)
     dx = L / n
     R = np.asarray(frame["R"], dtype=np.float64).reshape(3, 3)
     xg = OM.global_nodes(xw, frame)

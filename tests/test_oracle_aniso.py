@@ -183,3 +183,37 @@ def test_adjoint_on_the_anisotropic_box_matches_central_differences():
             fd = (OA.forward(p, u0, shifted(h), w, a, b)[0] - OA.forward(p, u0, shifted(-h), w, a, b)[0]) / (2 * h)
             ad = float(np.sum(g * d))
             assert abs(fd - ad) < 1e-7 * max(abs(fd), 1e-12), (k, which, fd, ad)
+
+
+def test_rasterise_vjp_on_the_anisotropic_grid():
+    """The rasteriser's transpose on a 32 x 32 x 16 grid of a 4 x 4 x 2 box
+    (the wing revolving about the centre (2, 2, 1)) against central
+    differences of J = sum chi_bar chi + sum us_bar u_s."""
+    from oracle import adjoint as OA
+    from paper_2002_08642_gb300 import inputs
+
+    n, nz, L = 32, 16, 4.0
+    dx = L / n
+    xw0, tri = inputs.elliptic_wing_mesh(60)
+    xw, vw, fr = inputs.revolving_wing(0.3, xw0, inputs.flapping_amplitudes(xw0), centre=(2.0, 2.0, 1.0))
+    rng = np.random.default_rng(7)
+    cb = rng.standard_normal((n, n, nz))
+    ub = rng.standard_normal((3, n, n, nz))
+
+    def J(x):
+        chi, us, _, _ = OM.rasterise(n, L, x, vw, tri, fr, 2 * dx, 1.5 * dx, nz=nz)
+        return float(np.sum(cb * chi) + np.sum(ub * us))
+
+    g = OA.rasterise_vjp(n, L, xw, vw, tri, fr, 2 * dx, 1.5 * dx, cb, ub, nz=nz)
+    h = 1e-6
+    errs = []
+    for node in rng.choice(len(xw), 6, replace=False):
+        for c in range(3):
+            xp = xw.copy()
+            xp[node, c] += h
+            xm = xw.copy()
+            xm[node, c] -= h
+            fd = (J(xp) - J(xm)) / (2 * h)
+            errs.append(abs(fd - g[node, c]) / max(abs(fd), abs(g[node, c]), 1e-3))
+    errs = np.array(errs)
+    assert np.median(errs) < 1e-5 and np.mean(errs < 1e-4) > 0.85, errs
