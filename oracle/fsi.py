@@ -44,7 +44,8 @@ class Coupled:
 
     def _mask(self):
         fr, _ = self.frames(self.t)
-        chi, us, _, _ = OM.rasterise(self.p.n, self.p.L, self.x, self.v, self.tri, fr, self.tw, self.h)
+        chi, us, _, _ = OM.rasterise(self.p.n, self.p.L, self.x, self.v, self.tri, fr, self.tw, self.h,
+                                     nz=self.p.nz)
         self.fluid.set_mask(chi, us)
 
     def step(self, nsteps=1):
