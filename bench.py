@@ -37,6 +37,24 @@ WORKLOADS = {
 CPU_SAMPLE_N = 48
 
 
+
+def fma_peak(precision, iters, stream_ptr):
+    """Measured FMA rate (FLOP/s) of the current device from the bench-only
+    probe library libps_bench.so; precision 0 = FP32, 1 = FP64."""
+    import ctypes
+
+    from paper_2002_08642_gb300 import build as pbuild
+
+    lib = ctypes.CDLL(pbuild.BENCH_LIB)
+    fn = lib.bench_fma_peak
+    fn.restype = ctypes.c_int32
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double(0.0)
+    st = fn(int(precision), int(iters), ctypes.c_void_p(stream_ptr), ctypes.byref(out))
+    if st != 0:
+        raise RuntimeError("bench_fma_peak failed with status %d" % st)
+    return out.value
+
 def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4):
     """Bytes each pass must move per step with the 2/3-truncated storage
     (reads + writes of the kept modes only), keyed by pass name."""
@@ -325,10 +343,8 @@ def run_ours(args, cfg):
     # the z pass against the FP32 FMA rate: its line transforms (4.5 complex
     # length-n transforms per (x, y) line, 5 n log2 n FLOPs each) and the
     # pointwise term; it is bound by instruction issue, not by FMA throughput
-    from paper_2002_08642_gb300 import binding as PB
-
     z_ms = passes["z_c2r_nonlinear_r2c"][0] / max(passes["z_c2r_nonlinear_r2c"][1], 1)
-    peak32 = PB.ps_fma_peak(PB.PS_FP32 if cfg["precision"] == "fp32" else PB.PS_FP64, 200000, stream.cuda_stream)
+    peak32 = fma_peak(0 if cfg["precision"] == "fp32" else 1, 200000, stream.cuda_stream)
     z_fl = 4.5 * n * n * 5.0 * n * math.log2(n) + 15.0 * n ** 3
     z_pass_alu = {"bound": "alu", "achieved": z_fl / (z_ms / 1e3) / 1e12, "peak": peak32 / 1e12,
                   "unit": "TFLOP/s", "frac": z_fl / (z_ms / 1e3) / peak32, "flops_per_launch": z_fl,
@@ -426,9 +442,7 @@ def run_ours(args, cfg):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         v64 = n ** 3 * k64 / (ms64 / 1e3) / 1e6
-        from paper_2002_08642_gb300 import binding as PB
-
-        peak64 = PB.ps_fma_peak(PB.PS_FP64, 20000, stream.cuda_stream)
+        peak64 = fma_peak(1, 20000, stream.cuda_stream)
         fl = step_flops(n)
         out["fp64_step"] = {"value": v64, "unit": "Mpts*steps/s", "steps": k64, "ms_per_step": ms64 / k64,
                             "fp32_speedup": value / v64,

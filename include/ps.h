@@ -256,10 +256,12 @@ ps_status ps_timing_read(ps_ctx* ctx, double* ms, int64_t* launches, int32_t cap
 const char* ps_timing_name(int32_t i);
 
 /* Penalization force and moment of caller-supplied physical fields, for
- * callers that cannot allocate device memory (code inside someone else's
- * CUDA-graph capture, host callbacks, allocation-free real-time loops): it
- * needs no ps_ctx and no workspace. The paper has no counterpart; it is the
- * force reduction of ps_step (F = (dx^3/eta) sum chi (u - u_s),
+ * callers that must not allocate device memory after start-up: a real-time
+ * loop (cudaMalloc can block and synchronise the device), a process whose
+ * framework's memory pool already holds nearly all device memory (a fresh
+ * cudaMalloc fails there), code under a no-dynamic-allocation rule. It needs
+ * no ps_ctx and no workspace. The paper has no counterpart; it is the force
+ * reduction of ps_step (F = (dx^3/eta) sum chi (u - u_s),
  * M = (dx^3/eta) sum (x - x0) x chi (u - u_s), x = (i, j, k) dx) offered alone.
  *   n, precision, L, eta, x0  grid size, PS_FP32/PS_FP64 (type of the real
  *              arrays), box length, penalization constant, moment point
@@ -271,9 +273,13 @@ const char* ps_timing_name(int32_t i);
  * Scratch lives in a fixed 48 KiB array compiled into the library (one
  * partial per x-plane, 1024 planes): n > 1024 returns PS_EINVAL. Nothing is
  * allocated: no cudaMalloc, no cudaFree. The first call on each device looks
- * up the array's device address; make it before any stream capture. Calls
- * share the array: two calls that may overlap on the GPU (unordered streams)
- * race. Returns PS_ECUDA if a launch fails. */
+ * up the array's device address and caches it; after cudaDeviceReset that
+ * address is stale and the call must not be used again. Calls share the
+ * array: two calls that may overlap on the GPU (unordered streams) race.
+ * It makes CUDA calls, so it must not be called from a stream callback or a
+ * host function (cudaLaunchHostFunc). Returns PS_ECUDA, leaving the error in
+ * place, if an error from earlier work is pending on entry, and PS_ECUDA if
+ * one of its own launches fails. */
 ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision, double L, double eta,
                                         const double x0[3], const void* u_dev, const void* chi_dev,
                                         const void* us_dev, double* FM_dev, void* cuda_stream);
@@ -281,13 +287,6 @@ ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision, double L, 
 /* Text of the last error on this context ("" if none). */
 const char* ps_last_error(const ps_ctx* ctx);
 
-/* Measured fused multiply-add rate of the current device in FLOP/s (an FMA
- * counts 2), PS_FP32 or PS_FP64: 8 blocks of 256 threads per SM, each thread
- * 8 independent FMA chains of `iters` steps, timed with CUDA events on
- * cuda_stream after one warm-up launch. Synchronises. It is the arithmetic
- * ceiling the FP64 step is measured against (no counterpart in the paper).
- * PS_EINVAL for a bad precision or iters < 1; PS_ECUDA if a launch fails. */
-ps_status ps_fma_peak(int32_t precision, int32_t iters, void* cuda_stream, double* flops_per_s);
 
 /* ------------------------------------------------------------------------
  * Mass-spring network of the wing (Sec. 2.1-2.2). Host code, host memory,

@@ -73,7 +73,6 @@ _SIGS = {
     "ps_last_error": (ctypes.c_char_p, [c_void_p]),
     "ps_penalization_force_noalloc": (c_int32, [c_int32, c_int32, c_double, c_double, _P(c_double), c_void_p,
                                                 c_void_p, c_void_p, c_void_p, c_void_p]),
-    "ps_fma_peak": (c_int32, [c_int32, c_int32, c_void_p, _P(c_double)]),
     "ps_ms_create": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                                c_int32, c_void_p, c_void_p, _P(c_void_p)]),
     "ps_ms_destroy": (c_int32, [c_void_p]),
@@ -277,14 +276,6 @@ def make_frame(fr):
     return f
 
 
-def ps_fma_peak(precision, iters, stream_ptr):
-    """Measured FMA rate of the current device, FLOP/s."""
-    out = c_double(0.0)
-    check(lib().ps_fma_peak(int(precision), int(iters), c_void_p(stream_ptr), ctypes.byref(out)))
-    return out.value
-
-
-# ------------------------------------------------------------- mass-spring
 def ms_check(status, m):
     if status != PS_OK:
         raw = lib().ps_ms_last_error(m) if m else None

@@ -3,6 +3,9 @@
 Translation units are compiled in parallel, one -gencode for sm_103a, then
 linked into ``paper_2002_08642_gb300/_build/libps.so``. A rebuild happens
 only when a source or header is newer than the library.
+
+``libps_bench.so`` (same folder) holds measurement tooling that bench.py
+uses (the device's FMA rate); it is not part of the solver's ABI.
 """
 import os
 import subprocess
@@ -14,7 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libps.so")
-SOURCES = ["ps_api.cu", "ps_f32.cu", "ps_f64.cu", "ps_noalloc.cu", "ps_massspring.cu", "ps_peak.cu"]
+BENCH_LIB = os.path.join(OUT_DIR, "libps_bench.so")
+SOURCES = ["ps_api.cu", "ps_f32.cu", "ps_f64.cu", "ps_noalloc.cu", "ps_massspring.cu"]
+BENCH_SOURCES = ["bench_fma_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]
@@ -35,9 +40,9 @@ def _inputs():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(BENCH_LIB):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(BENCH_LIB))
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -58,16 +63,20 @@ def build(force=False, verbose=False, extra_flags=()):
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr[-8000:]))
-    os.replace(tmp, LIB)
-    return LIB
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + len(BENCH_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + BENCH_SOURCES))
 
+    def link(out, parts):
+        tmp = out + ".tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *parts, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr[-8000:]))
+        os.replace(tmp, out)
+
+    link(LIB, objs[:len(SOURCES)])
+    link(BENCH_LIB, objs[len(SOURCES):])
+    return LIB
 
 if __name__ == "__main__":
     import sys

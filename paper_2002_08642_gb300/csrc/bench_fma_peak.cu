@@ -1,7 +1,9 @@
-// ps_peak.cu -- measured fused multiply-add rate of the current device, the
-// ALU ceiling that the FP64 step is held against (the FP64 path moves half
-// the bytes per second of the FP32 path but runs several times slower, so
-// on this part it is bound by FP64 arithmetic, not by HBM).
+// bench_fma_peak.cu -- measurement tooling for bench.py, built into its own
+// libps_bench.so and not part of the solver library's ABI (include/ps.h).
+// It measures the fused multiply-add rate of the current device, the ALU
+// ceiling that the FP64 step is held against (the FP64 path moves half the
+// bytes per second of the FP32 path but runs several times slower, so on
+// this part it is bound by FP64 arithmetic, not by HBM).
 //
 // Each thread runs 8 independent FMA chains for `iters` iterations (8
 // chains hide the FMA latency); the grid is 8 blocks of 256 threads per SM.
@@ -10,7 +12,11 @@
 // live.
 #include <cuda_runtime.h>
 
-#include "ps.h"
+#include <stdint.h>
+
+// status codes as in include/ps.h
+enum { kOk = 0, kEinval = 1, kEcuda = 3 };
+enum { kFp32 = 0, kFp64 = 1 };
 
 static __device__ double ps_peak_sink;
 
@@ -27,25 +33,28 @@ __global__ void __launch_bounds__(256) k_fma_chains(int iters, T seed) {
     if (s == (T)-1.2345e30) ps_peak_sink = (double)s;
 }
 
-extern "C" ps_status ps_fma_peak(int32_t precision, int32_t iters, void* cuda_stream, double* flops_per_s) {
-    if (!flops_per_s || iters < 1 || (precision != PS_FP32 && precision != PS_FP64)) return PS_EINVAL;
+// FLOP/s (an FMA counts 2) of k_fma_chains in `precision` (0 FP32, 1 FP64):
+// 8 blocks of 256 threads per SM, timed with CUDA events on cuda_stream
+// after one warm-up launch. Synchronises.
+extern "C" int32_t bench_fma_peak(int32_t precision, int32_t iters, void* cuda_stream, double* flops_per_s) {
+    if (!flops_per_s || iters < 1 || (precision != kFp32 && precision != kFp64)) return kEinval;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return PS_ECUDA;
+        return kEcuda;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int blocks = 8 * nsm, threads = 256;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return PS_ECUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess) return kEcuda;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
-        return PS_ECUDA;
+        return kEcuda;
     }
     float ms = 0.0f;
     cudaError_t err = cudaSuccess;
     for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // the first launch warms up
         cudaEventRecord(e0, s);
-        if (precision == PS_FP64) k_fma_chains<double><<<blocks, threads, 0, s>>>(iters, 1.0);
+        if (precision == kFp64) k_fma_chains<double><<<blocks, threads, 0, s>>>(iters, 1.0);
         else k_fma_chains<float><<<blocks, threads, 0, s>>>(iters, 1.0f);
         cudaEventRecord(e1, s);
         err = cudaEventSynchronize(e1);
@@ -54,7 +63,7 @@ extern "C" ps_status ps_fma_peak(int32_t precision, int32_t iters, void* cuda_st
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (err != cudaSuccess || !(ms > 0.0f)) return PS_ECUDA;
+    if (err != cudaSuccess || !(ms > 0.0f)) return kEcuda;
     *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
-    return PS_OK;
+    return kOk;
 }

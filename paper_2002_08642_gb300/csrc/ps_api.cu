@@ -29,10 +29,6 @@ struct ps_ctx {
     int fp64;
     const Ops* ops;
     int zblocks;        // force partials written by the z pass
-    int nslab;          // slabs of the y/z/y pipeline
-    cudaStream_t aux[2];
-    cudaEvent_t sev[3];
-    bool aux_ok;
     KP kp;
     Bufs b;
     size_t elem;        // bytes of one real
@@ -47,7 +43,6 @@ struct ps_ctx {
     CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
     CUtensorMap tmG;          // adjoint G (x-inverse input), with_adjoint only
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
-    CUtensorMap tmBo;         // B in y-forward boxes of the slab pipeline
     CUtensorMap tmN;          // keep_uw: the pressure's N fields (y-forward input)
     bool uw_valid;            // keep_uw: B holds u and omega of the current state
     // adjoint (with_adjoint): lam, mu, G, W, Ub, Wb spectral; u, w, nb physical
@@ -523,17 +518,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm < 1) nsm = 1;
-    cudaError_t e = ops->prepare(nsm, &c->zblocks, &c->nslab);
-    if (e == cudaSuccess && c->nslab > 1) {
-        if ((e = cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking)) == cudaSuccess &&
-            (e = cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&c->sev[0], cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&c->sev[1], cudaEventDisableTiming)) == cudaSuccess &&
-            (e = cudaEventCreateWithFlags(&c->sev[2], cudaEventDisableTiming)) == cudaSuccess)
-            c->aux_ok = true;
-        for (int i = 0; i < 2; ++i) c->b.aux[i] = c->aux[i];
-        for (int i = 0; i < 3; ++i) c->b.sev[i] = c->sev[i];
-    }
+    cudaError_t e = ops->prepare(nsm, &c->zblocks);
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
         if (!encode_planes(&c->tmA, c->b.A, c->fp64, kp.Kzp, (size_t)n, (size_t)6 * Kk, ops->cy2, ops->br2) ||
@@ -541,8 +526,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
             !encode_rows(&c->tmU, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2) ||
             !encode_rows(&c->tmA5, c->b.A, c->fp64, (size_t)6 * Kk * n, kp.Kzp, ops->cx5, ops->br4) ||
             !encode_rows(&c->tmUp, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
-            !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
-            !encode_rows(&c->tmBo, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4o, ops->br4)) {
+            !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2)) {
             delete c;
             return PS_ECUDA;
         }
@@ -552,7 +536,6 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         c->b.tmA5 = &c->tmA5;
         c->b.tmUp = &c->tmUp;
         c->b.tmHp = &c->tmHp;
-        c->b.tmBo = &c->tmBo;
         c->b.tmG = nullptr;
         c->b.chi_sp = nullptr;
         if (p->with_adjoint) {
@@ -589,12 +572,6 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
 ps_status ps_destroy(ps_ctx* c) {
     if (!c) return PS_EINVAL;
     for (cudaEvent_t ev : c->tev_step) cudaEventDestroy(ev);
-    if (c->aux_ok) {
-        cudaStreamSynchronize(c->aux[0]);
-        cudaStreamSynchronize(c->aux[1]);
-        for (int i = 0; i < 2; ++i) cudaStreamDestroy(c->aux[i]);
-        for (int i = 0; i < 3; ++i) cudaEventDestroy(c->sev[i]);
-    }
     for (cudaEvent_t ev : c->tev_mask) cudaEventDestroy(ev);
     delete c;
     return PS_OK;
@@ -933,15 +910,10 @@ ps_status ps_timing_read(ps_ctx* c, double* ms, int64_t* launches, int32_t cap, 
         *acc += t;
         return true;
     };
-    const int S = c->nslab > 1 ? c->nslab : 1;
     for (long k = 0; k < ns; ++k) {
         cudaEvent_t* ev = &c->tev_step[(size_t)k * kEvPerStep];
-        bool ok = el(ev[0], ev[1], &ms[0]);
-        for (int sl = 0; sl < S && ok; ++sl) {
-            cudaEvent_t* e = ev + 2 + 6 * sl;
-            ok = el(e[0], e[1], &ms[1]) && el(e[2], e[3], &ms[2]) && el(e[4], e[5], &ms[3]);
-        }
-        ok = ok && el(ev[2 + 6 * kMaxSlabs], ev[3 + 6 * kMaxSlabs], &ms[4]);
+        bool ok = true;
+        for (int i = 0; i < 5 && ok; ++i) ok = el(ev[2 * i], ev[2 * i + 1], &ms[i]);
         if (!ok) return fail(c, PS_ECUDA, "ps_timing_read");
         for (int i = 0; i < 5; ++i) launches[i] += 1;
     }

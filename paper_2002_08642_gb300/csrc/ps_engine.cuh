@@ -4,22 +4,6 @@
 #pragma once
 #include "ps_kernels.cuh"
 
-#ifndef PS_X1_OLD
-#define PS_X1_OLD 0
-#endif
-#ifndef PS_X5_OLD
-#define PS_X5_OLD 0
-#endif
-// slab pipeline: the y/z/y passes run over PS_SLABS x slabs alternating on
-// two auxiliary streams, so the compute-bound z pass of one slab overlaps the
-// memory-bound y passes of its neighbours (1 = plain serial passes)
-#ifndef PS_SLABS
-#define PS_SLABS 1   // measured on GB300: no gain from overlapping (kept switchable)
-#endif
-#ifndef PS_OVL_ZB
-#define PS_OVL_ZB 1
-#endif
-
 namespace ps {
 
 struct Bufs {
@@ -41,28 +25,21 @@ struct Bufs {
     const CUtensorMap* tmA5; // A as rows of 2 Kzp reals (x-forward input)
     const CUtensorMap* tmUp; // U, H as rows of 2 Kzp reals, x-forward box (L2 prefetch)
     const CUtensorMap* tmHp;
-    const CUtensorMap* tmBo; // B, y-forward box of the slab pipeline
     const CUtensorMap* tmG;  // adjoint G as rows of 2 Kzp reals, x-inverse box (null without adjoint)
     const void* chi_sp;      // sponge mask (n^3, caller-owned), null when the sponge term is off
     void* N3;                // keep_uw: 3 z-spectral fields [f][x][y][kz] for the pressure's N (else null)
     const CUtensorMap* tmN;  // N3 as rows of 2 Kzp reals (y-forward input), keep_uw only
-    cudaStream_t aux[2];     // slab pipeline streams
-    cudaEvent_t sev[3];      // fork/join events of the slab pipeline
 };
 
-// Timing events of one step: P1 start/end, then per slab (up to kMaxSlabs)
-// start/end of P2, P3, P4, then P5 start/end.
-static constexpr int kMaxSlabs = 8;
-static constexpr int kEvPerStep = 4 + 6 * kMaxSlabs;
+// Timing events of one step: start/end of P1, P2, P3, P4, P5.
+static constexpr int kEvPerStep = 10;
 
 struct Ops {
     int n, C, C5, LY, G;
     int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
-    int cy4o;                 // y-forward box width in the slab pipeline
     int cx1, cx5;             // TMA box widths of the x passes (heights br2, br4)
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
-    cudaError_t (*prepare)(int nsm, int* zblocks, int* nslab);
-    int nslab;    // slabs of the y/z/y pipeline (set by prepare)
+    cudaError_t (*prepare)(int nsm, int* zblocks);
     // ev (nullable): kEvPerStep events (see kEvPerStep)
     cudaError_t (*step)(const KP&, const Bufs&, int first, int resume, cudaStream_t, cudaEvent_t* ev);
     cudaError_t (*set_velocity)(const KP&, const Bufs&, const void* u, cudaStream_t);
@@ -130,26 +107,7 @@ template <typename T, int N> struct Engine {
     static constexpr int thr_y2 = GE::CY2 * GE::G;
     static constexpr int thr_y4 = GE::CY4 * GE::G;
 
-    static int& nslab() {
-        static int v = 1;
-        return v;
-    }
-    static int& ovl_z() {
-        static int v = 1;
-        return v;
-    }
-    static int& ovl_y2() {
-        static int v = 1;
-        return v;
-    }
-    static int& ovl_y4() {
-        static int v = 1;
-        return v;
-    }
-    static constexpr size_t sm_y4o = (size_t)GE::y4_smem(GE::CY4O);
-    static constexpr int thr_y4o = GE::CY4O * GE::G;
-
-    static cudaError_t prepare(int nsm, int* zb, int* ns) {
+    static cudaError_t prepare(int nsm, int* zb) {
         cudaError_t e;
         if ((e = attr(k_xinv<T, N, 6>, sm_strided))) return e;
         if ((e = attr(k_xinv<T, N, 3>, sm_strided))) return e;
@@ -174,7 +132,6 @@ template <typename T, int N> struct Engine {
         *zb = zgrid();
         if ((e = attr(k_yinv_tma<T, N>, sm_y2))) return e;
         if ((e = attr(k_yfwd_tma<T, N, GE::CY4>, sm_y4))) return e;
-        if ((e = attr(k_yfwd_tma<T, N, GE::CY4O>, sm_y4o))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yinv_tma<T, N>, thr_y2, sm_y2))) return e;
         y2grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N, GE::CY4>, thr_y4, sm_y4))) return e;
@@ -197,17 +154,6 @@ template <typename T, int N> struct Engine {
         x1grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
         x5grid() = nsm * (occ < 1 ? 1 : occ);
-        // slab pipeline: x slabs of whole z-pass batches, one block per SM per kernel
-        int S = PS_SLABS;
-        if (S > kMaxSlabs) S = kMaxSlabs;
-        while (S > 1 && (N % S != 0 || ((N / S) * N) % GE::LZ != 0)) S /= 2;
-        if (N < 128) S = 1;
-        nslab() = S;
-        ovl_z() = nsm * PS_OVL_ZB;
-        ovl_y2() = nsm;
-        ovl_y4() = nsm;
-        *ns = S;
-        if (S > 1) *zb = S * ovl_z();
         return cudaSuccess;
     }
 
@@ -221,83 +167,34 @@ template <typename T, int N> struct Engine {
     // 2 are skipped; their timing events are recorded back to back
     static cudaError_t step(const KP& kp, const Bufs& b, int first, int resume, cudaStream_t s, cudaEvent_t* ev) {
         const C2* tw = (const C2*)b.tw;
+        KP k1 = kp;
+        k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
+        const bool sp = b.chi_sp != nullptr;   // sponge term: six-field z/y-forward variants
         if (ev) cudaEventRecord(ev[0], s);
-        if (!resume) {
-#if PS_X1_OLD
-            k_xinv<T, N, 6><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
-#else
-            k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
-#endif
-        }
-        if (ev) cudaEventRecord(ev[1], s);
-        const int S = b.chi_sp ? 1 : nslab();   // the sponge variant runs the plain serial passes
-        if (b.chi_sp) {
-            KP k1 = kp;
-            k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-            if (ev) cudaEventRecord(ev[2], s);
-            if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
-            if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
+        if (!resume) k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
+        if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
+        if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
+        if (sp)
             k_zpass<T, N, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                                      b.flag, b.partial, tw, b.err, nullptr,
                                                                      (const T*)b.chi_sp, (C2*)b.B);
-            if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
-            k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
-            if (ev) cudaEventRecord(ev[7], s);
-            if (ev) cudaEventRecord(ev[2 + 6 * kMaxSlabs], s);
+        else
+            k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+                                                        b.partial, tw, b.err, nullptr, nullptr, (C2*)b.B);
+        if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
+        if (sp) k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        else k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        if (ev) { cudaEventRecord(ev[7], s); cudaEventRecord(ev[8], s); }
+        if (sp)
             k_xfwd_tma<T, N, 0, true><<<x5sgrid(), thr_x5, sm_x5s, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
                                                                        (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez,
                                                                        first, tw, b.err);
-            if (ev) cudaEventRecord(ev[3 + 6 * kMaxSlabs], s);
-            return cudaGetLastError();
-        }
-        if (S <= 1) {
-            KP k1 = kp;
-            k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-            if (ev) cudaEventRecord(ev[2], s);
-            if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
-            if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
-            k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                        b.flag, b.partial, tw, b.err, nullptr, nullptr, (C2*)b.B);
-            if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
-            k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
-            if (ev) cudaEventRecord(ev[7], s);
-        } else {
-            // fork: both auxiliary streams wait for the x-inverse
-            cudaEventRecord(b.sev[0], s);
-            cudaStreamWaitEvent(b.aux[0], b.sev[0], 0);
-            cudaStreamWaitEvent(b.aux[1], b.sev[0], 0);
-            for (int sl = 0; sl < S; ++sl) {
-                cudaStream_t st = b.aux[sl & 1];
-                KP k1 = kp;
-                k1.xs0 = sl * (N / S);
-                k1.xsn = N / S;
-                k1.part_off = sl * ovl_z();
-                cudaEvent_t* e = ev ? ev + 2 + 6 * sl : nullptr;
-                if (e) cudaEventRecord(e[0], st);
-                if (!resume) k_yinv_tma<T, N><<<ovl_y2(), thr_y2, sm_y2, st>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
-                if (e) { cudaEventRecord(e[1], st); cudaEventRecord(e[2], st); }
-                k_zpass<T, N><<<ovl_z(), thr_zp, sm_zp, st>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                             b.flag, b.partial, tw, b.err, nullptr, nullptr,
-                                                             (C2*)b.B);
-                if (e) { cudaEventRecord(e[3], st); cudaEventRecord(e[4], st); }
-                k_yfwd_tma<T, N, GE::CY4O><<<ovl_y4(), thr_y4o, sm_y4o, st>>>(*b.tmBo, k1, (C2*)b.A, tw, b.err);
-                if (e) cudaEventRecord(e[5], st);
-            }
-            // join
-            cudaEventRecord(b.sev[1], b.aux[0]);
-            cudaEventRecord(b.sev[2], b.aux[1]);
-            cudaStreamWaitEvent(s, b.sev[1], 0);
-            cudaStreamWaitEvent(s, b.sev[2], 0);
-        }
-        if (ev) cudaEventRecord(ev[2 + 6 * kMaxSlabs], s);
-#if PS_X5_OLD
-        k_xfwd<T, N, 0><<<grid_xs(kp, GE::C5), thr_5, sm_x5, s>>>(kp, (const C2*)b.A, (C2*)b.U, (C2*)b.H,
-                                                                 (const T*)b.Ex, (const T*)b.Ez, first, tw);
-#else
-        k_xfwd_tma<T, N, 0><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
-                                                            (const T*)b.Ex, (const T*)b.Ez, first, tw, b.err);
-#endif
-        if (ev) cudaEventRecord(ev[3 + 6 * kMaxSlabs], s);
+        else
+            k_xfwd_tma<T, N, 0><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
+                                                                (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez, first, tw,
+                                                                b.err);
+        if (ev) cudaEventRecord(ev[9], s);
         return cudaGetLastError();
     }
 
@@ -399,8 +296,6 @@ template <typename T, int N> struct Engine {
         o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
         o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
         o.cx1 = GE::CX1; o.cx5 = GE::CX5;
-        o.cy4o = GE::CY4O;
-        o.nslab = 1;
         o.zblocks = 0;
         o.prepare = &prepare;
         o.step = &step;

@@ -87,9 +87,6 @@
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
 #endif
-#ifndef PS_Y4O_SMEM_KB
-#define PS_Y4O_SMEM_KB 120
-#endif
 
 #include "ps_async.cuh"
 #include "ps_fft.cuh"
@@ -225,8 +222,6 @@ template <typename T, int N> struct Geo {
     static constexpr int CY4 = pick_c(4, PS_Y4_SMEM_KB, 16);
     static constexpr int CX1 = pick_c(1, PS_X1_SMEM_KB, 16);   // same smem shape as the y inverse, two buffers
     static constexpr int CX5 = pick_c(5, PS_X5_SMEM_KB, 128 / 16);
-    // y-forward tile when it shares SMs with the z pass (slab pipeline)
-    static constexpr int CY4O = pick_c(4, PS_Y4O_SMEM_KB, 16);
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
 

@@ -1,26 +1,35 @@
 // ps_noalloc.cu -- penalization force and moment of caller-supplied fields
 // without any device allocation.
 //
-// Who needs this: code that runs where cudaMalloc is not an option -- inside
-// a CUDA-graph capture another library owns, in a host callback, under a
-// memory pool that forbids new allocations, or in a real-time loop that must
-// never block on the allocator. Such callers cannot create a ps_ctx (its
-// workspace is caller memory sized in the gigabytes) just to reduce a force.
-// This entry point keeps its only scratch -- one partial sum per x-plane --
-// in a fixed array compiled into the library.
+// Who needs this: callers that must not call cudaMalloc after start-up.
+// Examples:
+//   * a real-time control loop: cudaMalloc can block and synchronise the
+//     device;
+//   * a process whose framework's memory pool already holds nearly all
+//     device memory, where a fresh cudaMalloc fails;
+//   * code under a no-dynamic-allocation rule.
+// Such callers cannot create a ps_ctx, whose workspace is gigabytes of
+// caller memory, just to reduce a force. This entry point keeps its only
+// scratch, one partial sum per x-plane, in a fixed array compiled into the
+// library.
 //
 // The scratch: ps_noalloc_partials, 1024 planes x 6 doubles (48 KiB) per
 // device that loads the library, held until the process exits. Grids with
 // n > 1024 are rejected (PS_EINVAL). Each call writes every partial it later
-// reads, so no state carries over between calls; but calls share the array,
-// so two calls whose kernels overlap on the GPU (different streams, no
-// ordering between them) race and must not be issued.
+// reads, so nothing carries over between calls. But all calls share the
+// array: two calls whose kernels overlap on the GPU (different streams, no
+// ordering between them) race, and must not be issued.
 //
 // Device-address set-up: host code cannot pass the array's name to a kernel
-// (on the host it is only a stand-in symbol), so the first call on each
+// (on the host it is only a stand-in symbol). So the first call on each
 // device, with that device current, looks the address up with
-// cudaGetSymbolAddress and caches it. Make that first call before any stream
-// capture begins.
+// cudaGetSymbolAddress and caches it per device number. The cached address
+// belongs to the device's current context: after cudaDeviceReset it is
+// stale, and the call must not be used again in that process.
+//
+// It makes CUDA runtime calls (launches, error queries), so it must not be
+// called from a stream callback or a host function queued with
+// cudaLaunchHostFunc: CUDA forbids CUDA calls there.
 #include <mutex>
 
 #include "ps.h"
@@ -83,6 +92,9 @@ extern "C" ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision,
     if (n < 1 || n > kNoallocMaxPlanes) return PS_EINVAL;
     if (precision != PS_FP32 && precision != PS_FP64) return PS_EINVAL;
     if (!(L > 0) || !(eta > 0) || !x0 || !u_dev || !chi_dev || !us_dev || !FM_dev) return PS_EINVAL;
+    // an error left by earlier work on this thread stays in place for the
+    // code that caused it; this call does not start on top of it
+    if (cudaPeekAtLastError() != cudaSuccess) return PS_ECUDA;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return PS_ECUDA;
     double* part = nullptr;
@@ -97,12 +109,15 @@ extern "C" ps_status ps_penalization_force_noalloc(int32_t n, int32_t precision,
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const double dx = L / n;
+    // each launch checked on its own (a failed launch's error is this call's)
     if (precision == PS_FP64)
         k_force_planes<double><<<n, 256, 0, s>>>(n, dx, x0[0], x0[1], x0[2], (const double*)u_dev,
                                                  (const double*)chi_dev, (const double*)us_dev, part);
     else
         k_force_planes<float><<<n, 256, 0, s>>>(n, dx, x0[0], x0[1], x0[2], (const float*)u_dev,
                                                 (const float*)chi_dev, (const float*)us_dev, part);
+    if (cudaGetLastError() != cudaSuccess) return PS_ECUDA;
     k_force_planes_final<<<1, 32, 0, s>>>(n, dx * dx * dx / eta, part, FM_dev);
-    return cudaGetLastError() == cudaSuccess ? PS_OK : PS_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return PS_ECUDA;
+    return PS_OK;
 }

@@ -113,7 +113,7 @@ def test_keep_uw_resume_is_bitwise_identical(n, prec):
     """keep_uw: the step after ps_pressure starts at its z pass with the u
     and omega the pressure left in B. The coupling order (step, pressure,
     new mask, step, pressure twice, step) gives the same bits as a context
-    that runs every pass (128^3 runs the y/z/y slab pipeline)."""
+    that runs every pass."""
     L, nu, eta, dt = 4.0, 1.527e-4, 1e-2, 5e-4
     dtype = torch.float64 if prec == "fp64" else torch.float32
     xw0, tri = inputs.elliptic_wing_mesh(300)
