@@ -16,8 +16,9 @@
  * - Real-valued device arrays use the context's precision: float for
  *   PS_FP32, double for PS_FP64 ("real" below). Force, moment, diagnostics,
  *   node coordinates and frames are always double.
- * - Physical fields are C-order [ix][iy][iz] (z fastest), n^3 values per
- *   component, components stored one after another (3*n^3 for a vector).
+ * - Physical fields are C-order [ix][iy][iz] (z fastest) on the n x n x nz
+ *   grid (ps_params.nz, n for a cubic grid), n^2 nz values per component,
+ *   components stored one after another (3 n^2 nz for a vector).
  * - The context allocates NO device memory: the caller passes one workspace
  *   of ps_workspace_size() bytes (256-byte aligned) to ps_init and keeps it
  *   alive until ps_destroy.
@@ -58,8 +59,15 @@ enum { PS_MEAN_FIXED = 0, PS_MEAN_FREE = 1 };
 /*
  * Solver parameters (Sec. 4.1, Eq. penalized Navier--Stokes; the paper's
  * C_eta is eta here).
- *   n          points per axis of the periodic n^3 grid on [0, L)^3; the
- *              library supports the sizes listed by ps_supported_n().
+ *   n          points along x and y of the periodic n x n x nz grid on
+ *              [0, L)^2 x [0, Lz); the library supports the sizes listed
+ *              by ps_supported_n().
+ *   nz         points along z: 0 or n (cubic box, Lz = L), or n/2 for
+ *              n >= 32 (Lz = L/2: the 4 x 4 x 2 box with N x N x N/2 points
+ *              of the paper's revolving-wing runs, Sec. 4.2). The spacing
+ *              L/n is the same on every axis; z wavenumbers are 2 pi m/Lz
+ *              and the 2/3 rule keeps 3|m_z| < nz. Other values return
+ *              PS_EUNSUPPORTED.
  *   precision  PS_FP32: transforms, nonlinear term, projection and update in
  *              float, force/moment/diagnostic reductions in double;
  *              PS_FP64: everything in double.
@@ -76,7 +84,7 @@ enum { PS_MEAN_FIXED = 0, PS_MEAN_FREE = 1 };
  *   tw, h      wing semi-thickness and smoothing semi-width of the mask.
  *   x0         reference point of the moment.
  *   keep_uw    1: the workspace also holds three z-spectral fields
- *              (3 n^2 Kzp complex, Kzp = (n-1)/3 + 1 rounded up to 16 (FP32)
+ *              (3 n^2 Kzp complex, Kzp = (nz-1)/3 + 1 rounded up to 16 (FP32)
  *              or 8 (FP64) values) so that ps_pressure keeps u and omega of the
  *              state it evaluated; a ps_step right after it (nothing between
  *              that changes the velocity) then starts at its z pass and skips
@@ -94,6 +102,7 @@ typedef struct {
     double tw, h;
     double x0[3];
     int32_t keep_uw;
+    int32_t nz;
 } ps_params;
 
 /* Wing frame -> global frame (Sec. 4.1, Eq. relative_velocities):
@@ -121,7 +130,7 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev,
                   size_t workspace_bytes, ps_ctx** out);
 ps_status ps_destroy(ps_ctx* ctx);
 
-/* Velocity u (3*n^3 real, physical, caller device memory). ps_set_velocity
+/* Velocity u (3 n^2 nz real, physical, caller device memory). ps_set_velocity
  * transforms it, truncates it by the 2/3 rule and projects it onto
  * divergence-free fields (mean kept); the Adams--Bashforth history restarts,
  * so the next step is an integrating-factor Euler step. ps_get_velocity
@@ -129,12 +138,12 @@ ps_status ps_destroy(ps_ctx* ctx);
 ps_status ps_set_velocity(ps_ctx* ctx, const void* u_dev);
 ps_status ps_get_velocity(ps_ctx* ctx, void* u_dev_out);
 
-/* Dense mask chi (n^3 real in [0,1]) and solid velocity u_s (3*n^3 real),
+/* Dense mask chi (n^2 nz real in [0,1]) and solid velocity u_s (3 n^2 nz real),
  * caller device memory, copied into the workspace (Sec. 4.1: chi and u_s of
  * the penalization term). */
 ps_status ps_set_mask(ps_ctx* ctx, const void* chi_dev, const void* us_dev);
 
-/* Copy the current mask chi (n^3 real) and solid velocity u_s (3*n^3 real)
+/* Copy the current mask chi (n^2 nz real) and solid velocity u_s (3 n^2 nz real)
  * into caller device memory. */
 ps_status ps_get_mask(ps_ctx* ctx, void* chi_dev_out, void* us_dev_out);
 
@@ -160,6 +169,19 @@ ps_status ps_step(ps_ctx* ctx, int32_t nsteps);
  * the last step taken (Sec. 4.2.2 defines lift and drag from this force).
  * Host outputs; synchronises the stream. */
 ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
+/* Device error flag. Every wait of a kernel on its asynchronous copies has
+ * an iteration cap; a wait that gives up sets the context's device error
+ * flag, lets the copies it started land, and ends the kernel early, so the
+ * results of that launch are invalid. ps_forces then returns PS_ECUDA. The
+ * flag is sticky: every later ps_forces fails too, until ps_clear_error
+ * resets it (synchronises the stream). */
+ps_status ps_clear_error(ps_ctx* ctx);
+/* Test hook for the error path above (no counterpart in the paper): one
+ * block waits, with an iteration cap of `cap` polls (>= 1), on an mbarrier
+ * that expects 16 bytes of bulk copy that no copy delivers (none is
+ * issued), gives up and sets the device error flag like a transform pass.
+ * Nothing stays in flight. Synchronises. PS_EINVAL for cap < 1. */
+ps_status ps_debug_wait_timeout(ps_ctx* ctx, int32_t cap);
 
 /* Sponge term (Sec. 4.1, Eq. penalized Navier--Stokes: the vorticity
  * damping term), added to the nonlinear term of every following step:
@@ -167,7 +189,7 @@ ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
  * s_hat the 2/3-truncated transform of chi_sp omega. (The paper prints the
  * term with 1/lap and a minus sign, which read literally amplifies; the
  * damping form its text describes is taken: for chi_sp = 1, S = -u/C_sp.)
- *   chi_sp_dev  n^3 array [x][y][z] in the context precision, caller-owned;
+ *   chi_sp_dev  n^2 nz array [x][y][z] in the context precision, caller-owned;
  *               read by every step while set, so it must stay valid and
  *               unchanged until the sponge is turned off. NULL turns it off.
  *   c_sp        C_sp > 0 (ignored when turning off).
@@ -181,7 +203,7 @@ ps_status ps_set_sponge(ps_ctx* ctx, const void* chi_sp_dev, double c_sp);
  * form; the fluid-solid coupling computes p^{n+1} from u^{n+1}). Pi is the
  * gradient part the Leray projection removes from the nonlinear and
  * penalization term N: Pi_hat = -i (k . N_hat)/|k|^2, mean zero.
- *   p_dev  caller-owned n^3 array [x][y][z] in the context precision.
+ *   p_dev  caller-owned n^2 nz array [x][y][z] in the context precision.
  * Costs about one time step (the step's passes 1-4, then one inverse
  * field). Leaves the state and the forces of ps_forces unchanged; uses the
  * internal scratch arrays. With keep_uw the x and y passes it ran are not
@@ -196,7 +218,7 @@ ps_status ps_pressure(ps_ctx* ctx, void* p_dev);
  * the unit box, five points per axis, periodic), and
  * F_v = -p_v sum over the triangles T containing v of (A_T/3) n_T, n_T the
  * unit normal (b - a) x (c - a)/|...| of T's vertex order, global frame.
- *   p_dev        n^3 pressure from ps_pressure (context precision)
+ *   p_dev        n^2 nz pressure from ps_pressure (context precision)
  *   xw_dev, tri_dev, frame  as in ps_set_mask_from_nodes
  *   p_nodes_dev  n_nodes doubles out; f_nodes_dev n_nodes x 3 doubles out
  * All device pointers caller-owned; sums in double. Asynchronous. */
@@ -227,7 +249,7 @@ ps_status ps_restore_state(ps_ctx* ctx, const void* buf_dev);
  * the forward state u^n (use ps_restore_state / ps_step to get there) and the
  * mask chi^n, u_s^n of that step; dJdF = a_n, dJdM = b_n (host, 3 doubles
  * each); first = 1 if step n was the integrating-factor Euler start step.
- * It overwrites grad_chi_dev (n^3 real) and grad_us_dev (3*n^3 real) with
+ * It overwrites grad_chi_dev (n^2 nz real) and grad_us_dev (3 n^2 nz real) with
  * dJ/dchi^n and dJ/du_s^n and updates the adjoint state. Asynchronous. */
 ps_status ps_adjoint_reset(ps_ctx* ctx);
 ps_status ps_adjoint_step(ps_ctx* ctx, const double dJdF[3], const double dJdM[3], int32_t first,
@@ -266,7 +288,8 @@ const char* ps_timing_name(int32_t i);
  *   n, precision, L, eta, x0  grid size, PS_FP32/PS_FP64 (type of the real
  *              arrays), box length, penalization constant, moment point
  *              (host array of 3 doubles)
- *   u_dev (3*n^3), chi_dev (n^3), us_dev (3*n^3)  physical fields, layout as
+ *   u_dev (3*n^3), chi_dev (n^3), us_dev (3*n^3)  physical fields of a cubic
+ *              n^3 grid, layout as
  *              everywhere in this header
  *   FM_dev     device output, 6 doubles: F then M
  *   cuda_stream  stream the work is enqueued on (asynchronous)

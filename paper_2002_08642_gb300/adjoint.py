@@ -21,7 +21,7 @@ class WingWindow:
         self.disp = disp        # list of (n_nodes, 3) float64 cuda
         self.vw = vw            # list of (n_nodes, 3) float64 cuda
         self.frames = frames    # list of frame dicts
-        self.u0 = u0            # (3, n, n, n) cuda, solver dtype
+        self.u0 = u0            # (3, n, n, nz) cuda, solver dtype
         self.steps = len(frames)
 
 
@@ -55,9 +55,9 @@ class TimeAveragedForce(torch.autograd.Function):
         K = win.steps
         g = gout.detach().double().cpu().numpy() / K
         a, b = g[:3], g[3:]
-        n = solver.n
-        gchi = torch.empty((n, n, n), dtype=solver.dtype, device=solver.device)
-        gus = torch.empty((3, n, n, n), dtype=solver.dtype, device=solver.device)
+        n, nz = solver.n, solver.nz
+        gchi = torch.empty((n, n, nz), dtype=solver.dtype, device=solver.device)
+        gus = torch.empty((3, n, n, nz), dtype=solver.dtype, device=solver.device)
         gxw = torch.zeros_like(xw0, dtype=torch.float64)
         solver.adjoint_reset()
         starts = sorted(ckpts)

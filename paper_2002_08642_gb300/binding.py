@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "PS_OK", 1: "PS_EINVAL", 2: "PS_ENOMEM", 3: "PS_ECUDA", 4: "P
 class PsParams(ctypes.Structure):
     _fields_ = [("n", c_int32), ("precision", c_int32), ("mask_profile", c_int32), ("mean_mode", c_int32),
                 ("with_adjoint", c_int32), ("L", c_double), ("nu", c_double), ("eta", c_double), ("dt", c_double),
-                ("tw", c_double), ("h", c_double), ("x0", c_double * 3), ("keep_uw", c_int32)]
+                ("tw", c_double), ("h", c_double), ("x0", c_double * 3), ("keep_uw", c_int32),
+                ("nz", c_int32)]
 
 
 class PsFrame(ctypes.Structure):
@@ -57,6 +58,8 @@ _SIGS = {
     "ps_step": (c_int32, [c_void_p, c_int32]),
     "ps_forces": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_diagnostics": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
+    "ps_clear_error": (c_int32, [c_void_p]),
+    "ps_debug_wait_timeout": (c_int32, [c_void_p, c_int32]),
     "ps_pressure": (c_int32, [c_void_p, c_void_p]),
     "ps_set_sponge": (c_int32, [c_void_p, c_void_p, c_double]),
     "ps_pressure_loads": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_int32, _P(PsFrame),
@@ -206,6 +209,14 @@ def ps_diagnostics(ctx):
     st = lib().ps_diagnostics(ctx, ctypes.byref(e), ctypes.byref(d))
     check(st, ctx)
     return e.value, d.value
+
+
+def ps_clear_error(ctx):
+    check(lib().ps_clear_error(ctx), ctx)
+
+
+def ps_debug_wait_timeout(ctx, cap):
+    check(lib().ps_debug_wait_timeout(ctx, int(cap)), ctx)
 
 
 def ps_state_size(ctx):

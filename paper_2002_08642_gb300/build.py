@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libps.so")
 BENCH_LIB = os.path.join(OUT_DIR, "libps_bench.so")
-SOURCES = ["ps_api.cu", "ps_f32.cu", "ps_f64.cu", "ps_noalloc.cu", "ps_massspring.cu"]
+SOURCES = ["ps_api.cu", "ps_f32_a.cu", "ps_f32_b.cu", "ps_f64_a.cu", "ps_f64_b.cu", "ps_noalloc.cu", "ps_massspring.cu"]
 BENCH_SOURCES = ["bench_fma_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -35,7 +35,7 @@ __global__ void k_adj_spec1(KP kp, cplx<T>* __restrict__ lam, cplx<T>* __restric
     const int K = kp.K, Kz = kp.Kz, Kzp = kp.Kzp, mm = kp.mmax;
     const size_t FS = (size_t)K * K * Kzp;
     const size_t tot = (size_t)K * K * Kz;
-    const T dt = (T)kp.dt, s = (T)kp.ks;
+    const T dt = (T)kp.dt, s = (T)kp.ks, sz = (T)kp.ksz;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
         const int cz = (int)(i % Kz);
         const size_t r = i / Kz;
@@ -51,7 +51,7 @@ __global__ void k_adj_spec1(KP kp, cplx<T>* __restrict__ lam, cplx<T>* __restric
             g[f] = cmk<C2>(a1 * l[f].x + m.x, a1 * l[f].y + m.y);
         }
         const int mx = cmode_of(cx, mm, K), my = cmode_of(cy, mm, K);
-        const T kx = s * (T)mx, ky = s * (T)my, kz = s * (T)cz;
+        const T kx = s * (T)mx, ky = s * (T)my, kz = sz * (T)cz;
         if (mx == 0 && my == 0 && cz == 0) {
             if (!kp.mean_free) g[0] = g[1] = g[2] = cmk<C2>((T)0, (T)0);
         } else {
@@ -78,14 +78,14 @@ __global__ void k_adj_spec2(KP kp, cplx<T>* __restrict__ lam, const cplx<T>* __r
     const int K = kp.K, Kz = kp.Kz, Kzp = kp.Kzp, mm = kp.mmax;
     const size_t FS = (size_t)K * K * Kzp;
     const size_t tot = (size_t)K * K * Kz;
-    const T s = (T)kp.ks;
+    const T s = (T)kp.ks, sz = (T)kp.ksz;
     const T n3 = (T)(1.0 / kp.invn3);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
         const int cz = (int)(i % Kz);
         const size_t r = i / Kz;
         const int cx = (int)(r % K), cy = (int)(r / K);
         const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
-        const T kx = s * (T)cmode_of(cx, mm, K), ky = s * (T)cmode_of(cy, mm, K), kz = s * (T)cz;
+        const T kx = s * (T)cmode_of(cx, mm, K), ky = s * (T)cmode_of(cy, mm, K), kz = sz * (T)cz;
         const C2 wx = Wb[o], wy = Wb[FS + o], wz = Wb[2 * FS + o];
         const C2 c0 = cmk<C2>(ky * wz.x - kz * wy.x, ky * wz.y - kz * wy.y);
         const C2 c1 = cmk<C2>(kz * wx.x - kx * wz.x, kz * wx.y - kx * wz.y);
@@ -105,8 +105,9 @@ __global__ void k_adj_spec2(KP kp, cplx<T>* __restrict__ lam, const cplx<T>* __r
 template <typename T>
 __global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w, const T* __restrict__ nb,
                             const T* __restrict__ chi, const T* __restrict__ us, T* __restrict__ gchi,
-                            T* __restrict__ gus, int n) {
-    const size_t n3 = (size_t)n * n * n;
+                            T* __restrict__ gus) {
+    const int n = kp.n, nz = kp.nz;
+    const size_t n3 = (size_t)n * n * nz;
     // constants in T: no double arithmetic and no 64-bit division per point
     const T inv_eta = (T)kp.inv_eta, invn3 = (T)kp.invn3, dx = (T)kp.dx;
     const T f = (T)(kp.dx * kp.dx * kp.dx * kp.inv_eta);
@@ -114,10 +115,10 @@ __global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w
     const T a0 = (T)aw.a[0], a1 = (T)aw.a[1], a2 = (T)aw.a[2];
     const T b0 = (T)aw.b[0], b1 = (T)aw.b[1], b2 = (T)aw.b[2];
     // 32-bit point index (n^3 < 2^32 for every built grid size)
-    const uint32_t n3u = (uint32_t)n3, un = (uint32_t)n;
+    const uint32_t n3u = (uint32_t)n3, un = (uint32_t)n, unz = (uint32_t)nz;
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n3u; p += gridDim.x * blockDim.x) {
         {
-            const uint32_t q = p / un, k = p - q * un;
+            const uint32_t q = p / unz, k = p - q * unz;
             const uint32_t i = q / un, j = q - i * un;
             const T rx = (T)i * dx - x0, ry = (T)j * dx - y0;
             const T nbx = nb[p] * invn3, nby = nb[n3 + p] * invn3, nbz = nb[2 * n3 + p] * invn3;
@@ -169,8 +170,8 @@ __device__ __forceinline__ double chi_profile_d(double d, double tw, double h, i
 template <typename T>
 __device__ void vjp_point(const MaskWs& m, const MaskArgs& a, uint32_t p, int t, const T* __restrict__ gchi,
                           const T* __restrict__ gus, const T* __restrict__ chi, double* __restrict__ gX) {
-    const size_t n = a.n, n3 = n * n * n;
-    const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+    const size_t n = a.n, nz = a.nz, n3 = n * n * nz;
+    const int k = (int)(p % nz), j = (int)((p / nz) % n), i = (int)(p / (n * nz));
     const double P[3] = {i * a.dx, j * a.dx, k * a.dx};
     const int id[3] = {a.tri[3 * t], a.tri[3 * t + 1], a.tri[3 * t + 2]};
     double X[3][3];
@@ -270,9 +271,9 @@ __global__ void k_mask_vjp_list(MaskWs m, MaskArgs a, int par, const T* __restri
 template <typename T>
 __global__ void k_mask_vjp_dense(MaskWs m, MaskArgs a, const T* __restrict__ gchi, const T* __restrict__ gus,
                                  const T* __restrict__ chi, double* __restrict__ gX) {
-    const size_t n = a.n, n3 = n * n * n;
+    const size_t n = a.n, nz = a.nz, n3 = n * n * nz;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+        const int k = (int)(p % nz), j = (int)((p / nz) % n), i = (int)(p / (n * nz));
         T best = (T)3.0e38;
         int bt = -1;
         for (int t = 0; t < a.n_tri; ++t) {

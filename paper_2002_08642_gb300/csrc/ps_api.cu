@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -77,15 +78,17 @@ struct Layout {
 };
 
 int mmax_of(int n) { return (n - 1) / 3; }
+// points along z (0 means n)
+int nz_of(const ps_params* p) { return p->nz == 0 ? p->n : p->nz; }
 
 bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
-    const int n = p->n;
+    const int n = p->n, nz = nz_of(p);
     const int fp64 = p->precision == PS_FP64;
     const size_t er = fp64 ? 8 : 4, ec = 2 * er;
-    const int mm = mmax_of(n), K = 2 * mm + 1, Kz = mm + 1;
+    const int mm = mmax_of(n), K = 2 * mm + 1, Kz = mmax_of(nz) + 1;
     const int Cw = tile_width(fp64);
     const int Kzp = (Kz + Cw - 1) / Cw * Cw;
-    const size_t n3 = (size_t)n * n * n;
+    const size_t n3 = (size_t)n * n * nz;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L->ustate = 3 * (size_t)K * K * Kzp * ec;
@@ -97,14 +100,16 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
     L->chi = take(n3 * er);
     L->us = take(3 * n3 * er);
     L->flag = take((size_t)n * n);
-    L->tw = take((size_t)3 * n * ec);   // n-line table, then (n = 3M) the M-line table at n and e^{2 pi i b q/n} at 2n
+    // n-line table, then (n = 3M) the M-line table at n and e^{2 pi i b q/n}
+    // at 2n; for nz != n the same three for nz-lines from 3n on
+    L->tw = take((size_t)3 * (n + nz) * ec);
     L->Ex = take((size_t)K * er);
     L->Ez = take((size_t)Kz * er);
     const size_t nparts = (size_t)n * n + 4096;
     L->partial = take(nparts * 6 * sizeof(double));
     L->out = take(64 * sizeof(double));
     L->err = take(256);
-    L->mask_bytes = mask_workspace_bytes(n);
+    L->mask_bytes = mask_workspace_bytes(n, nz);
     L->mask = take(L->mask_bytes);
     // lam, mu, G, (unused), Ub, Wb
     for (int i = 0; i < 6; ++i) L->adj_spec[i] = p->with_adjoint && i != 3 ? take(L->ustate) : 0;
@@ -115,7 +120,10 @@ bool layout_for(const ps_params* p, const Ops* ops, Layout* L) {
 }
 
 const Ops* ops_for(const ps_params* p) {
-    return p->precision == PS_FP64 ? ops_f64(p->n) : ops_f32(p->n);
+    const int nz = nz_of(p);
+    const Ops* o = p->precision == PS_FP64 ? ops_f64_a(p->n, nz) : ops_f32_a(p->n, nz);
+    if (!o) o = p->precision == PS_FP64 ? ops_f64_b(p->n, nz) : ops_f32_b(p->n, nz);
+    return o;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
@@ -183,7 +191,11 @@ ps_status check_params(const ps_params* p, std::string* why) {
         *why = "L, eta, dt, h must be > 0 and nu, tw >= 0";
         return PS_EINVAL;
     }
-    if (!ops_for(p)) { *why = "grid size n=" + std::to_string(p->n) + " is not built into libps"; return PS_EUNSUPPORTED; }
+    if (p->nz < 0) { *why = "nz must be >= 0"; return PS_EINVAL; }
+    if (!ops_for(p)) {
+        *why = "grid size n=" + std::to_string(p->n) + ", nz=" + std::to_string(nz_of(p)) + " is not built into libps";
+        return PS_EUNSUPPORTED;
+    }
     return PS_OK;
 }
 
@@ -212,8 +224,8 @@ template <typename T>
 void host_tables(const ps_params* p, std::vector<unsigned char>& tw, std::vector<unsigned char>& ex,
                  std::vector<unsigned char>& ez) {
     using C2 = cplx<T>;
-    const int n = p->n, mm = mmax_of(n), K = 2 * mm + 1, Kz = mm + 1;
-    std::vector<C2> t((size_t)3 * n, cmk<C2>((T)0, (T)0));
+    const int n = p->n, nz = nz_of(p), mm = mmax_of(n), K = 2 * mm + 1, Kz = mmax_of(nz) + 1;
+    std::vector<C2> t((size_t)3 * (n + nz), cmk<C2>((T)0, (T)0));
     // stage twiddles of a length-m line at offset `base`
     auto line_table = [&](int m, size_t base) {
         const int S = n_stages(m);
@@ -227,37 +239,44 @@ void host_tables(const ps_params* p, std::vector<unsigned char>& tw, std::vector
                 }
         }
     };
-    line_table(n, 0);
-    if (n % 3 == 0) {
-        const int M = n / 3;
-        line_table(M, (size_t)n);
-        for (int b = 1; b <= 2; ++b)
-            for (int q = 0; q < M; ++q) {
-                double c, sn;
-                unit_root((long)b * q, (long)n, &c, &sn);
-                t[(size_t)2 * n + (b - 1) * M + q] = cmk<C2>((T)c, (T)sn);
-            }
-    }
+    // the table of length-m lines at `base`: the stage twiddles, then for
+    // m = 3M the M-line table at base + m and e^{2 pi i b q/m} at base + 2m
+    auto tables = [&](int m, size_t base) {
+        line_table(m, base);
+        if (m % 3 == 0) {
+            const int M = m / 3;
+            line_table(M, base + (size_t)m);
+            for (int b = 1; b <= 2; ++b)
+                for (int q = 0; q < M; ++q) {
+                    double c, sn;
+                    unit_root((long)b * q, (long)m, &c, &sn);
+                    t[base + (size_t)2 * m + (b - 1) * M + q] = cmk<C2>((T)c, (T)sn);
+                }
+        }
+    };
+    tables(n, 0);
+    if (nz != n) tables(nz, (size_t)3 * n);
     tw.assign((unsigned char*)t.data(), (unsigned char*)(t.data() + t.size()));
     const double ks = 2.0 * M_PI / p->L;
+    const double ksz = ks * (double)n / (double)nz;   // 2 pi / Lz, Lz = L nz / n
     std::vector<T> vx(K), vz(Kz);
     for (int c = 0; c < K; ++c) {
         const int m = c <= mm ? c : c - K;
         vx[c] = (T)exp(-p->nu * (ks * m) * (ks * m) * p->dt);
     }
-    for (int c = 0; c < Kz; ++c) vz[c] = (T)exp(-p->nu * (ks * c) * (ks * c) * p->dt);
+    for (int c = 0; c < Kz; ++c) vz[c] = (T)exp(-p->nu * (ksz * c) * (ksz * c) * p->dt);
     ex.assign((unsigned char*)vx.data(), (unsigned char*)(vx.data() + K));
     ez.assign((unsigned char*)vz.data(), (unsigned char*)(vz.data() + Kz));
 }
 
 // ------------------------------------------------------ generic kernels
 template <typename T>
-__global__ void k_line_flags(const T* __restrict__ chi, uint8_t* __restrict__ flag, int n) {
+__global__ void k_line_flags(const T* __restrict__ chi, uint8_t* __restrict__ flag, int n, int nz) {
     const long line = (long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (line >= (long)n * n) return;
     int any = 0;
-    for (int z = lane; z < n; z += 32) any |= chi[line * n + z] != (T)0;
+    for (int z = lane; z < nz; z += 32) any |= chi[line * nz + z] != (T)0;
     any = __any_sync(0xffffffffu, any);
     if (lane == 0) flag[line] = (uint8_t)any;
 }
@@ -291,7 +310,7 @@ __global__ void k_diag(KP kp, const cplx<T>* __restrict__ U, double* __restrict_
         const size_t r = i / Kz;
         const int cy = (int)(r % K), cx = (int)(r / K);
         const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
-        const double kx = kp.ks * cmode_of(cx, mm, K), ky = kp.ks * cmode_of(cy, mm, K), kz = kp.ks * cz;
+        const double kx = kp.ks * cmode_of(cx, mm, K), ky = kp.ks * cmode_of(cy, mm, K), kz = kp.ksz * cz;
         double s = 0.0, dr = 0.0, di = 0.0;
         const double kk[3] = {kx, ky, kz};
         for (int f = 0; f < 3; ++f) {
@@ -318,6 +337,23 @@ __global__ void k_diag(KP kp, const cplx<T>* __restrict__ U, double* __restrict_
         for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, mx[w]);
         part[(size_t)blockIdx.x * 3 + 1] = m;
     }
+}
+
+// Test hook: an mbarrier that expects 16 bytes of bulk copy that no copy
+// delivers (none is issued), waited on with the kernels' bounded wait and a
+// caller-chosen cap; on giving up the block records the device error flag
+// the way the transform passes do. Nothing is in flight when it returns.
+__global__ void k_wait_timeout(int* __restrict__ err, uint32_t cap) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);
+    __syncthreads();
+    const bool ok = mbar_wait_cap(&bar, 0, cap);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
 __global__ void k_diag_final(const double* __restrict__ part, int nb, double half_L3, double* __restrict__ out) {
@@ -358,8 +394,8 @@ struct DeviceGuard {
 template <typename T>
 cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag, unsigned char* ws, int par, bool init,
                           bool dense_dirty, cudaStream_t s, int* par_out) {
-    const size_t n = a.n, n3 = n * n * n;
-    MaskWs m = mask_ws_split(ws, a.n);
+    const size_t n = a.n, n3 = n * n * a.nz;
+    MaskWs m = mask_ws_split(ws, a.n, a.nz);
     cudaError_t e;
     if (init) {
         if ((e = cudaMemsetAsync(m.key, 0xff, n3 * 8, s)) != cudaSuccess) return e;
@@ -420,7 +456,7 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
         pt_blocks = (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
     }
     k_adj_point<T><<<pt_blocks, 256, 0, s>>>(c->kp, aw, up, wp, np_, (const T*)c->b.chi, (const T*)c->b.us, (T*)gchi,
-                                          (T*)gus, c->p.n);
+                                          (T*)gus);
     if ((e = c->ops->fwd3(c->kp, c->b, up, Ub, s)) != cudaSuccess) return e;
     if ((e = c->ops->fwd3(c->kp, c->b, wp, Wb, s)) != cudaSuccess) return e;
     k_adj_spec2<T><<<nb, 256, 0, s>>>(c->kp, lam, Ub, Wb);
@@ -437,6 +473,7 @@ ps_status ps_supported_n(int32_t* out, int32_t cap, int32_t* count) {
 #undef PS_LIST
     };
     const int32_t total = (int32_t)(sizeof(sizes) / sizeof(sizes[0]));
+    std::sort(sizes, sizes + total);
     *count = total;
     if (out)
         for (int32_t i = 0; i < total && i < cap; ++i) out[i] = sizes[i];
@@ -476,19 +513,24 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     c->ops = ops;
     c->elem = c->fp64 ? 8 : 4;
     c->ustate = L.ustate;
-    const int n = p->n, mm = mmax_of(n);
+    const int n = p->n, nz = nz_of(p), mm = mmax_of(n);
+    c->p.nz = nz;
     KP& kp = c->kp;
+    kp.n = n;
+    kp.nz = nz;
     kp.mmax = mm;
     kp.K = 2 * mm + 1;
-    kp.Kz = mm + 1;
+    kp.Kz = mmax_of(nz) + 1;
     const int Cw = tile_width(c->fp64);
     kp.Kzp = (kp.Kz + Cw - 1) / Cw * Cw;
     kp.ks = 2.0 * M_PI / p->L;
+    const double Lz = p->L * (double)nz / (double)n;
+    kp.ksz = 2.0 * M_PI / Lz;
     kp.dt = p->dt;
     kp.inv_eta = 1.0 / p->eta;
-    kp.invn3 = 1.0 / ((double)n * n * n);
+    kp.invn3 = 1.0 / ((double)n * n * nz);
     kp.dx = p->L / n;
-    kp.half_L3 = 0.5 * p->L * p->L * p->L;
+    kp.half_L3 = 0.5 * p->L * p->L * Lz;
     for (int i = 0; i < 3; ++i) kp.x0[i] = p->x0[i];
     kp.mean_free = p->mean_mode == PS_MEAN_FREE;
 
@@ -604,15 +646,15 @@ ps_status ps_set_mask(ps_ctx* c, const void* chi, const void* us) {
     if (!chi || !us) return fail(c, PS_EINVAL, "ps_set_mask: null chi or us");
     DeviceGuard dg(c->device);
     const int n = c->p.n;
-    const size_t n3 = (size_t)n * n * n;
+    const size_t n3 = (size_t)n * n * c->p.nz;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(c->b.chi, chi, n3 * c->elem, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(c->b.us, us, 3 * n3 * c->elem, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ps_set_mask copy");
     const long lines = (long)n * n;
     const int per = 8;  // lines per block (one warp each)
-    if (c->fp64) k_line_flags<double><<<(unsigned)((lines + per - 1) / per), 32 * per, 0, c->stream>>>((const double*)c->b.chi, c->b.flag, n);
-    else k_line_flags<float><<<(unsigned)((lines + per - 1) / per), 32 * per, 0, c->stream>>>((const float*)c->b.chi, c->b.flag, n);
+    if (c->fp64) k_line_flags<double><<<(unsigned)((lines + per - 1) / per), 32 * per, 0, c->stream>>>((const double*)c->b.chi, c->b.flag, n, c->p.nz);
+    else k_line_flags<float><<<(unsigned)((lines + per - 1) / per), 32 * per, 0, c->stream>>>((const float*)c->b.chi, c->b.flag, n, c->p.nz);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ps_set_mask flags");
     c->mask_dense_dirty = true;
     c->has_last_mask = false;
@@ -624,7 +666,7 @@ ps_status ps_get_mask(ps_ctx* c, void* chi, void* us) {
     if (!chi || !us) return fail(c, PS_EINVAL, "ps_get_mask: null chi or us");
     DeviceGuard dg(c->device);
     const int n = c->p.n;
-    const size_t n3 = (size_t)n * n * n;
+    const size_t n3 = (size_t)n * n * c->p.nz;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(chi, c->b.chi, n3 * c->elem, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(us, c->b.us, 3 * n3 * c->elem, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
@@ -640,6 +682,7 @@ ps_status ps_set_mask_from_nodes(ps_ctx* c, const double* xw, const double* vw, 
     DeviceGuard dg(c->device);
     MaskArgs a;
     a.n = c->p.n;
+    a.nz = c->p.nz;
     a.dx = c->kp.dx;
     a.tw = c->p.tw;
     a.h = c->p.h;
@@ -727,6 +770,7 @@ ps_status ps_pressure_loads(ps_ctx* c, const void* p_dev, const double* xw, int3
     DeviceGuard dg(c->device);
     LoadArgs a;
     a.n = c->p.n;
+    a.nz = c->p.nz;
     a.dx = c->kp.dx;
     a.xw = xw;
     a.n_nodes = n_nodes;
@@ -762,6 +806,25 @@ ps_status ps_forces(ps_ctx* c, double F[3], double M[3]) {
     if (derr) return fail(c, PS_ECUDA, "a device-side copy wait gave up (results of the affected steps are invalid)");
     for (int i = 0; i < 3; ++i) { F[i] = h[i]; M[i] = h[3 + i]; }
     return PS_OK;
+}
+
+ps_status ps_clear_error(ps_ctx* c) {
+    if (!c) return PS_EINVAL;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaMemsetAsync(c->b.err, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_clear_error");
+    c->err.clear();
+    return sync(c, "ps_clear_error");
+}
+
+ps_status ps_debug_wait_timeout(ps_ctx* c, int32_t cap) {
+    if (!c) return PS_EINVAL;
+    if (cap < 1) return fail(c, PS_EINVAL, "ps_debug_wait_timeout: cap < 1");
+    DeviceGuard dg(c->device);
+    k_wait_timeout<<<1, 64, 0, c->stream>>>(c->b.err, (uint32_t)cap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_debug_wait_timeout");
+    return sync(c, "ps_debug_wait_timeout");
 }
 
 ps_status ps_diagnostics(ps_ctx* c, double* energy, double* max_div) {
@@ -861,7 +924,7 @@ ps_status ps_mask_nodes_vjp(ps_ctx* c, const void* grad_chi_dev, const void* gra
         return fail(c, PS_ESTATE, "ps_mask_nodes_vjp: the current mask did not come from ps_set_mask_from_nodes");
     DeviceGuard dg(c->device);
     const MaskArgs& a = c->last_mask;
-    MaskWs m = mask_ws_split(c->mask_ws, c->p.n);
+    MaskWs m = mask_ws_split(c->mask_ws, c->p.n, c->p.nz);
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->gX, 0, (size_t)a.n_nodes * 3 * sizeof(double), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ps_mask_nodes_vjp");

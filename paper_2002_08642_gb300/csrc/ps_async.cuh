@@ -52,11 +52,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity: false after the cap.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i)
+// Bounded wait for the phase with the given parity: false after `cap`
+// polls (each poll may itself suspend the thread for a short while).
+__device__ __forceinline__ bool mbar_wait_cap(uint64_t* bar, uint32_t parity, uint32_t cap) {
+    for (uint32_t i = 0; i < cap; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// The kernels' wait: 2^22 polls, far longer than any copy takes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_cap(bar, parity, 1u << 22);
 }
 
 }  // namespace ps

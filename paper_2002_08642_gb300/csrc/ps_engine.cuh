@@ -35,7 +35,7 @@ struct Bufs {
 static constexpr int kEvPerStep = 10;
 
 struct Ops {
-    int n, C, C5, LY, G;
+    int n, nz, C, C5, LY, G;
     int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
     int cx1, cx5;             // TMA box widths of the x passes (heights br2, br4)
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
@@ -56,18 +56,25 @@ struct Ops {
     cudaError_t (*pressure)(const KP&, const Bufs&, void* p, int resume, cudaStream_t);
 };
 
-template <typename T, int N> struct Engine {
+// N x N x NZ grid: the x and y passes are the kernels of length-N lines,
+// the z passes those of length-NZ lines (NZ = N, or N/2 for the 4 x 4 x 2
+// box); the z kernels take N at run time, so both grids share them.
+template <typename T, int N, int NZ = N> struct Engine {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
+    using GZ = Geo<T, NZ>;
     static constexpr size_t tw_bytes = (size_t)GE::tw_n * sizeof(C2);
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
-    static constexpr size_t sm_z = tw_bytes + (size_t)3 * GE::LY * GE::LP * sizeof(C2) / 2;
-    static constexpr size_t sm_zp = (size_t)GE::zsmem(GE::LZ);
+    static constexpr size_t sm_z = (size_t)GZ::tw_n * sizeof(C2) + (size_t)3 * GZ::LY * GZ::LP * sizeof(C2) / 2;
+    static constexpr size_t sm_zp = (size_t)GZ::zsmem(GZ::LZ);
     static constexpr int thr_s = GE::C * GE::G;
     static constexpr int thr_5 = GE::C5 * GE::G;
-    static constexpr int thr_z = GE::LY * GE::G;
-    static constexpr int thr_zp = 3 * GE::LZ * GE::G;
+    static constexpr int thr_z = GZ::LY * GZ::G;
+    static constexpr int thr_zp = 3 * GZ::LZ * GZ::G;
+    // twiddles of the z lines: the table of length-NZ lines sits after the
+    // length-N one when the lengths differ
+    static const C2* twz(const void* tw) { return (const C2*)tw + (NZ == N ? 0 : 3 * N); }
 
     template <class K> static cudaError_t attr(K k, size_t bytes) {
         return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -114,20 +121,20 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_yinv<T, N, 6>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 3>, sm_strided))) return e;
         if ((e = attr(k_yfwd<T, N>, sm_strided))) return e;
-        if ((e = attr(k_zpass<T, N>, sm_zp))) return e;
-        if ((e = attr(k_zpass<T, N, true>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ, true>, sm_zp))) return e;
         if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
-        if ((e = attr(k_zinv_phys<T, N, 1>, sm_z))) return e;
-        if ((e = attr(k_zfwd_phys<T, N>, sm_z))) return e;
-        if ((e = attr(k_zinv_phys<T, N>, sm_z))) return e;
+        if ((e = attr(k_zinv_phys<T, NZ, 1>, sm_z))) return e;
+        if ((e = attr(k_zfwd_phys<T, NZ>, sm_z))) return e;
+        if ((e = attr(k_zinv_phys<T, NZ>, sm_z))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 2>, sm_x5))) return e;
         int occ = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, N>, thr_zp, sm_zp))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, NZ>, thr_zp, sm_zp))) return e;
         if (occ < 1) occ = 1;
-        const int nb = N * N / GE::LZ;
+        const int nb = N * N / GZ::LZ;
         zgrid() = nsm * occ < nb ? nsm * occ : nb;
         *zb = zgrid();
         if ((e = attr(k_yinv_tma<T, N>, sm_y2))) return e;
@@ -145,7 +152,7 @@ template <typename T, int N> struct Engine {
         if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 3>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 0, true>, sm_x5s))) return e;
-        if ((e = attr(k_zpass<T, N, false, true>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ, false, true>, sm_zp))) return e;
         if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 6>, sm_y4))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, true>, thr_x5, sm_x5s)))
             return e;
@@ -159,7 +166,7 @@ template <typename T, int N> struct Engine {
 
     static dim3 grid_xs(const KP& kp, int C) { return dim3(kp.Kzp / C, kp.K); }
     static dim3 grid_ys(const KP& kp) { return dim3(kp.Kzp / GE::C, N); }
-    static int zblocks() { return N * N / GE::LY; }
+    static int zblocks() { return N * N / GZ::LY; }
 
 
     // resume: B already holds u and omega of the state (y-inverse output,
@@ -176,12 +183,12 @@ template <typename T, int N> struct Engine {
         if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
         if (sp)
-            k_zpass<T, N, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                                     b.flag, b.partial, tw, b.err, nullptr,
+            k_zpass<T, NZ, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+                                                                     b.flag, b.partial, twz(b.tw), b.err, nullptr,
                                                                      (const T*)b.chi_sp, (C2*)b.B);
         else
-            k_zpass<T, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
-                                                        b.partial, tw, b.err, nullptr, nullptr, (C2*)b.B);
+            k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+                                                        b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);
         if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
         if (sp) k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
         else k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
@@ -200,7 +207,7 @@ template <typename T, int N> struct Engine {
 
     static cudaError_t set_velocity(const KP& kp, const Bufs& b, const void* u, cudaStream_t s) {
         const C2* tw = (const C2*)b.tw;
-        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, tw);
+        k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, twz(b.tw));
         k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
         k_xfwd_tma<T, N, 1><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
@@ -211,7 +218,7 @@ template <typename T, int N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
         k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)u, tw);
+        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)u, twz(b.tw));
         return cudaGetLastError();
     }
 
@@ -219,7 +226,7 @@ template <typename T, int N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)spec, (C2*)b.A, tw);
         k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)phys, tw);
+        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)phys, twz(b.tw));
         return cudaGetLastError();
     }
 
@@ -227,7 +234,7 @@ template <typename T, int N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        k_zfwd_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const T*)phys, (C2*)b.B, tw);
+        k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const T*)phys, (C2*)b.B, twz(b.tw));
         k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
         k_xfwd_tma<T, N, 2><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, (C2*)spec, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
@@ -242,7 +249,7 @@ template <typename T, int N> struct Engine {
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         k_xinv_tma<T, N, 3><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmG, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N, 3><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
-        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)phys, tw);
+        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)phys, twz(b.tw));
         return cudaGetLastError();
     }
 
@@ -264,16 +271,16 @@ template <typename T, int N> struct Engine {
             k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         }
         C2* nout = b.N3 ? (C2*)b.N3 : (C2*)b.B;
-        k_zpass<T, N, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
-                                                          b.partial, tw, b.err, (T*)p, nullptr, nout);
+        k_zpass<T, NZ, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+                                                          b.partial, twz(b.tw), b.err, (T*)p, nullptr, nout);
         k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(b.N3 ? *b.tmN : *b.tmB, k1, (C2*)b.A, tw,
                                                                   b.err);
-        C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * GE::KZP;
+        C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * kp.Kzp;
         k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
         k_yinv_tma<T, N, 1><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
-        k_zinv_phys<T, N, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, tw);
+        k_zinv_phys<T, NZ, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw));
         return cudaGetLastError();
     }
 
@@ -286,14 +293,14 @@ template <typename T, int N> struct Engine {
         k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         const size_t BS = (size_t)N * N * k1.Kzp;
-        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, tw);
-        k_zinv_phys<T, N><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, tw);
+        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, twz(b.tw));
+        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, twz(b.tw));
         return cudaGetLastError();
     }
 
     static Ops ops() {
         Ops o;
-        o.n = N; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
+        o.n = N; o.nz = NZ; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
         o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
         o.cx1 = GE::CX1; o.cx5 = GE::CX5;
         o.zblocks = 0;
@@ -310,15 +317,35 @@ template <typename T, int N> struct Engine {
     }
 };
 
-// Grid sizes built into the library (a tuning build may restrict them).
-#ifdef PS_TUNING_SIZES
-#define PS_SIZES(X) X(256) X(768)
-#else
-#define PS_SIZES(X) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768)
-#endif
+// Grid sizes built into the library, as two halving chains so that every
+// N x N x N/2 engine is compiled in the translation unit that holds the
+// kernels of both of its line lengths.
+#define PS_SIZES_A(X) X(12) X(24) X(48) X(96) X(192) X(384) X(768)
+#define PS_SIZES_B(X) X(16) X(32) X(64) X(128) X(256) X(512)
+#define PS_SIZES(X) PS_SIZES_A(X) PS_SIZES_B(X)
+// smallest n with an N x N x N/2 engine
+static constexpr int kMinAnisoN = 32;
 
-// Defined in the per-precision translation units.
-const Ops* ops_f32(int n);
-const Ops* ops_f64(int n);
+// Engine of an n x n x nz grid of the built sizes (nz = n, or n/2 for
+// n >= kMinAnisoN), else null.
+template <typename T, int N> const Ops* ops_for_nz(int nz) {
+    if (nz == N) {
+        static const Ops o = Engine<T, N>::ops();
+        return &o;
+    }
+    if constexpr (N >= kMinAnisoN) {
+        if (2 * nz == N) {
+            static const Ops o = Engine<T, N, N / 2>::ops();
+            return &o;
+        }
+    }
+    return nullptr;
+}
+
+// Defined in the per-precision, per-chain translation units.
+const Ops* ops_f32_a(int n, int nz);
+const Ops* ops_f32_b(int n, int nz);
+const Ops* ops_f64_a(int n, int nz);
+const Ops* ops_f64_b(int n, int nz);
 
 }  // namespace ps

@@ -1,0 +1,18 @@
+// ps_f64_a.cu -- double instantiations of the step engine for the grid sizes
+// of chain A (cubic, and N x N x N/2 where N/2 is in the chain too).
+#include "ps_engine.cuh"
+
+namespace ps {
+
+#define PS_OPS_ENTRY(n) \
+    case n:             \
+        return ops_for_nz<double, n>(nz);
+
+const Ops* ops_f64_a(int n, int nz) {
+    switch (n) {
+        PS_SIZES_A(PS_OPS_ENTRY)
+        default: return nullptr;
+    }
+}
+
+}  // namespace ps

@@ -39,6 +39,17 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+
+// FP32 complex add and subtract as one packed two-lane instruction each
+// (sm_100 and later execute a float2 add as a single f32x2 operation; each
+// lane is rounded like the scalar add, so results are unchanged).
+#ifndef PS_F32X2
+#define PS_F32X2 1
+#endif
+#if PS_F32X2
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+#endif
 // a * (SIGN i)
 template <int SIGN, typename C> __device__ __forceinline__ C rot_i(C a) {
     if constexpr (SIGN > 0) return cmk<C>(-a.y, a.x);

@@ -94,8 +94,10 @@
 namespace ps {
 
 struct KP {
-    int mmax, K, Kz, Kzp;
+    int n, nz;        // points along x and y (n), along z (nz: n, or n/2 for the 4 x 4 x 2 box)
+    int mmax, K, Kz, Kzp;   // mmax, K from n; Kz = (nz - 1)/3 + 1 kept z modes, Kzp padded
     double ks;        // 2 pi / L
+    double ksz;       // 2 pi / Lz (Lz = L nz / n: the same spacing on every axis)
     double dt, inv_eta, invn3, dx, half_L3;
     double x0[3];
     int mean_free;
@@ -329,7 +331,7 @@ k_xinv(KP kp, const cplx<T>* __restrict__ U, cplx<T>* __restrict__ A, const cplx
     const int K = kp.K, mmax = kp.mmax, Kzp = kp.Kzp;
     const T ks = (T)kp.ks;   // wavenumbers in T: no double arithmetic per element
     const T ky = ks * (T)cmode_of(cy, mmax, K);
-    const T kz = ks * (T)cz;
+    const T kz = (T)kp.ksz * (T)cz;
     const size_t FS = (size_t)K * K * Kzp;
     const size_t AS = (size_t)N * K * Kzp;
     load_tw(tw, twg, GE::tw_n);
@@ -419,6 +421,8 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // [x][y][z]), leaves the force partials of the last step untouched and
 // writes its three result fields to Bo (Bo = B allowed), so that B can keep
 // u and omega of the state for the step that follows.
+// Template N is the z-line length (nz); the number of lines per x-plane
+// and the x-plane count are kp.n (n x n x nz grid).
 // SP (sponge term on): also s = chi_sp omega, transformed forward like n
 // (s_x + i s_y per line by the third thread group, s_z of line pairs by the
 // odd lines' second group, the groups that are otherwise idle) into B
@@ -440,7 +444,8 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     constexpr int GL = Z3 ? GM : G;
     constexpr bool WS = PS_ZWS != 0 && GL <= 32 && 32 % GL == 0;
     constexpr int TWM = Z3 ? (tw_count(M) > 0 ? tw_count(M) : 1) : 0;
-    const int b0 = kp.xs0 * N / LZ, b1 = (kp.xs0 + kp.xsn) * N / LZ;   // this launch's batches
+    const int nyl = kp.n;   // lines per x-plane (the line length is N)
+    const int b0 = kp.xs0 * nyl / LZ, b1 = (kp.xs0 + kp.xsn) * nyl / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int NB = GE::ZNB;
@@ -456,7 +461,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     const int fl = threadIdx.x / G, g = threadIdx.x % G;
     const int pl = fl / 3, pr = fl % 3;
     const int Kz = kp.Kz;
-    const size_t BS = (size_t)N * N * KZP;
+    const size_t BS = (size_t)nyl * nyl * KZP;
     auto tile = [&](int l, int p) { return tiles + (size_t)(l * 3 + p) * LP; };
     auto zad = [](int p) { return p + (p >> 4); };
     if (threadIdx.x == 0) {
@@ -483,7 +488,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     };
     if (threadIdx.x == 0 && b0 + (int)blockIdx.x < b1) issue(b0 + blockIdx.x, 0);
 
-    const size_t N3 = (size_t)N * N * N;
+    const size_t N3 = (size_t)nyl * nyl * N;
     const T inv_eta = (T)kp.inv_eta;
     int it = 0;
     for (int b = b0 + blockIdx.x; b < b1; b += gridDim.x, ++it) {
@@ -564,7 +569,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 const size_t po = (size_t)lid * N + z;
                 const T c = chi[po];
                 if (c != (T)0) {
-                    const int x = (int)(lid / N), y = (int)(lid % N);
+                    const int x = (int)(lid / nyl), y = (int)(lid % nyl);
                     const T sx = us[po], sy = us[N3 + po], sz = us[2 * N3 + po];
                     const T ce = c * inv_eta;
                     nx -= ce * (ux - sx);
@@ -770,7 +775,7 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         LineFFT<T, N, -1>::template run<false>(tile, tw, addr, g, load, store);
     }
     __syncthreads();
-    const T s = (T)kp.ks;
+    const T s = (T)kp.ks, sz = (T)kp.ksz;
     const T my = (T)cmode_of(cy, mmax, K);
     const T invn3 = (T)kp.invn3;
     const T dt = (T)kp.dt;
@@ -786,7 +791,7 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
         n0.x *= invn3; n0.y *= invn3;
         n1.x *= invn3; n1.y *= invn3;
         n2.x *= invn3; n2.y *= invn3;
-        const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+        const T kx = s * (T)mx, ky = s * my, kz = sz * (T)czz;
         const T k2 = kx * kx + ky * ky + kz * kz;
         const bool zero = (mx == 0 && cy == 0 && czz == 0);
         const size_t o = ((size_t)cy * K + cx) * Kzp + czz;
@@ -838,9 +843,9 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
            int* __restrict__ err) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
-    constexpr int CT = GE::CY2, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int CT = GE::CY2, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
-    constexpr int NTZ = KZP / CT;
+    const int KZP = kp.Kzp, NTZ = KZP / CT;
     const int NITEM = kp.xsn * NTZ * NF;  // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -924,10 +929,10 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
            int* __restrict__ err) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
-    constexpr int CT = CTV, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int CT = CTV, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "y-forward staging must be contiguous in y");
-    constexpr int NTZ = KZP / CT;
+    const int KZP = kp.Kzp, NTZ = KZP / CT;
     const int NITEM = kp.xsn * NTZ * NF;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1024,10 +1029,10 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     using FFT = LineFFT<T, N, 1>;
-    constexpr int CT = GE::CX1, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int CT = GE::CX1, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
-    constexpr int NTZ = KZP / CT;
-    constexpr int NTILE = K * NTZ;
+    const int KZP = kp.Kzp, NTZ = KZP / CT;
+    const int NTILE = K * NTZ;
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -1040,7 +1045,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     __shared__ __align__(8) uint64_t bar[2];
     const int col = threadIdx.x % CT, g = threadIdx.x / CT;
     const int mmax = kp.mmax, Kz = kp.Kz;
-    const T ks = (T)kp.ks;   // wavenumbers in T: no double arithmetic per element
+    const T ks = (T)kp.ks, ksz = (T)kp.ksz;   // wavenumbers in T: no double arithmetic per element
     const size_t AS = (size_t)N * K * KZP;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -1069,7 +1074,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         const T ky = ks * (T)cmode_of(cy, mmax, K);
-        const T kz = ks * (T)cz;
+        const T kz = ksz * (T)cz;
         C2* out = A + cz;   // + f AS + arow(x, cy) KZP
 #pragma unroll 1
         for (int f = 0; f < 3; ++f) {
@@ -1147,11 +1152,11 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
            int* __restrict__ err) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
-    constexpr int CT = GE::CX5, G = GE::G, K = GE::K, KZP = GE::KZP;
+    constexpr int CT = GE::CX5, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "x-forward staging must be contiguous in x");
-    constexpr int NTZ = KZP / CT;
-    constexpr int NTILE = K * NTZ;
+    const int KZP = kp.Kzp, NTZ = KZP / CT;
+    const int NTILE = K * NTZ;
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -1187,7 +1192,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             tma_load_2d(S + (size_t)(buf * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * K + cy) * N + b * BR, &bar[buf]);
     };
     if (threadIdx.x == 0) issue(0);
-    const T s = (T)kp.ks;
+    const T s = (T)kp.ks, sz = (T)kp.ksz;
     const T invn3 = (T)kp.invn3;
     const T dt = (T)kp.dt;
     int ti = 0;
@@ -1258,7 +1263,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
                     for (int idx = threadIdx.x; idx < K * CT; idx += blockDim.x) {
                         const int cx = idx / CT, czz = czt * CT + idx % CT;
                         const int mx = cmode_of(cx, mmax, K);
-                        const T kx = s * (T)mx, ky = s * myy, kz = s * (T)czz;
+                        const T kx = s * (T)mx, ky = s * myy, kz = sz * (T)czz;
                         const T k2 = kx * kx + ky * ky + kz * kz;
                         const C2 s0 = Rt[idx], s1 = Rt[K * CT + idx], s2 = Rt[2 * K * CT + idx];
                         const bool zero = (mx == 0 && cy == 0 && czz == 0);
@@ -1285,7 +1290,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             n0.x *= invn3; n0.y *= invn3;
             n1.x *= invn3; n1.y *= invn3;
             n2.x *= invn3; n2.y *= invn3;
-            const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+            const T kx = s * (T)mx, ky = s * my, kz = sz * (T)czz;
             const T k2 = kx * kx + ky * ky + kz * kz;
             const bool zero = (mx == 0 && cy == 0 && czz == 0);
             if (!zero) {
@@ -1323,7 +1328,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
             }
             if constexpr (MODE == 3) {   // Pi_hat = -i (k . N_hat) / |k|^2, Pi_hat(0) = 0
                 const int mx = cmode_of(cx, mmax, K);
-                const T kx = s * (T)mx, ky = s * my, kz = s * (T)czz;
+                const T kx = s * (T)mx, ky = s * my, kz = sz * (T)czz;
                 const T k2 = kx * kx + ky * ky + kz * kz;
                 const C2 n0 = Rt[idx], n1 = Rt[K * CT + idx], n2 = Rt[2 * K * CT + idx];
                 const T dr = (kx * n0.x + ky * n1.x + kz * n2.x) * invn3;
@@ -1356,7 +1361,8 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
 
 // ----------------------------------------------- physical <-> z-spectral
 // LY z lines per block, G threads per line (one warp or less: warp barriers
-// between FFT stages). Each line's (u_x + i u_y) is one complex transform;
+// between FFT stages). Template N is the z-line length (nz); there are
+// kp.n^2 lines. Each line's (u_x + i u_y) is one complex transform;
 // u_z of lines 2m and 2m + 1 share one, (u_z[2m] + i u_z[2m+1]).
 // Forward: physical u (3 x n^3 real) -> B fields 0..2 (z r2c, kz < Kz).
 template <typename T, int N>
@@ -1374,12 +1380,11 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
     C2* t1 = t0 + LY * LP;           // [LY / 2][LP]: u_z of each line pair
     const int line = threadIdx.x / G, g = threadIdx.x % G;
     const long lid = (long)blockIdx.x * LY + line;
-    const int x = (int)(lid / N), y = (int)(lid % N);
     const int Kz = kp.Kz, Kzp = kp.Kzp;
-    const size_t BS = (size_t)N * N * Kzp;
-    const size_t lo = ((size_t)x * N + y) * Kzp;
-    const size_t N3 = (size_t)N * N * N;
-    const size_t po = ((size_t)x * N + y) * N;
+    const size_t BS = (size_t)kp.n * kp.n * Kzp;
+    const size_t lo = (size_t)lid * Kzp;
+    const size_t N3 = (size_t)kp.n * kp.n * N;
+    const size_t po = (size_t)lid * N;
     load_tw(tw, twg, GE::tw_n);
     __syncthreads();
     {
@@ -1430,12 +1435,11 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     C2* tiles = tw + GE::tw_n;       // [LY][LP], reused by the two transforms
     const int line = threadIdx.x / G, g = threadIdx.x % G;
     const long lid = (long)blockIdx.x * LY + line;
-    const int x = (int)(lid / N), y = (int)(lid % N);
     const int Kz = kp.Kz, Kzp = kp.Kzp;
-    const size_t BS = (size_t)N * N * Kzp;
-    const size_t lo = ((size_t)x * N + y) * Kzp;
-    const size_t N3 = (size_t)N * N * N;
-    const size_t po = ((size_t)x * N + y) * N;
+    const size_t BS = (size_t)kp.n * kp.n * Kzp;
+    const size_t lo = (size_t)lid * Kzp;
+    const size_t N3 = (size_t)kp.n * kp.n * N;
+    const size_t po = (size_t)lid * N;
     load_tw(tw, twg, GE::tw_n);
     auto addr = [&](int p) { return zaddr(p, line, LP); };
     __syncthreads();
@@ -1455,7 +1459,7 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     if constexpr (MODE == 1) {
         // one field: thread group `line` takes the line pair (2 lid, 2 lid + 1)
         // (launched with half the blocks, rounded up)
-        const bool on = 2 * lid < (long)N * N;
+        const bool on = 2 * lid < (long)kp.n * kp.n;
         const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
         const C2* f0 = B + lo2;
         auto load = [&](int q) -> C2 { return two(f0, f0 + Kzp, q); };

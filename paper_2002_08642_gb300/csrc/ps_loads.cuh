@@ -16,7 +16,7 @@
 namespace ps {
 
 struct LoadArgs {
-    int n;
+    int n, nz;            // grid n x n x nz, spacing dx on every axis
     double dx;
     const double* xw;     // n_nodes x 3, wing frame
     int n_nodes;
@@ -52,16 +52,16 @@ __global__ void k_node_pressure(LoadArgs a, const T* __restrict__ pf, double* __
         lo[r] = (int)floor(g) - 2;
         for (int q = 0; q < 6; ++q) w[r][q] = delta_smoothed(g - (double)(lo[r] + q));
     }
-    const long n = a.n;
+    const long n = a.n, nz = a.nz;
     double acc = 0.0;
     for (int i = 0; i < 6; ++i) {
         const long xi = (((long)lo[0] + i) % n + n) % n;
         for (int j = 0; j < 6; ++j) {
             const long yj = (((long)lo[1] + j) % n + n) % n;
             const double wij = w[0][i] * w[1][j];
-            const T* row = pf + (xi * n + yj) * n;
+            const T* row = pf + (xi * n + yj) * nz;
             double s = 0.0;
-            for (int k = 0; k < 6; ++k) s += w[2][k] * (double)row[(((long)lo[2] + k) % n + n) % n];
+            for (int k = 0; k < 6; ++k) s += w[2][k] * (double)row[(((long)lo[2] + k) % nz + nz) % nz];
             acc += wij * s;
         }
     }

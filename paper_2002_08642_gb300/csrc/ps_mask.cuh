@@ -35,7 +35,7 @@
 namespace ps {
 
 struct MaskArgs {
-    int n;
+    int n, nz;   // grid n x n x nz, spacing dx on every axis
     double dx, tw, h;
     int profile;
     const double* xw;
@@ -61,8 +61,8 @@ static constexpr size_t kTriGeoBytes = 128;   // >= sizeof(TriGeo<double>)
 
 // Workspace: keys (8 B/pt), winner ids (4 B/pt), two touched lists (4 B/pt
 // each), counters, node and triangle scratch.
-inline size_t mask_workspace_bytes(int n) {
-    const size_t n3 = (size_t)n * n * n;
+inline size_t mask_workspace_bytes(int n, int nz) {
+    const size_t n3 = (size_t)n * n * nz;
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
     return a(n3 * 8) + a(n3 * 4) + 2 * a(n3 * 4) + a(64) + a((size_t)kMaskMaxNodes * 3 * 8) +
            a((size_t)kMaskMaxTri * 8 * 4) + a(((size_t)kMaskMaxTri + 1) * 8) + a((size_t)kMaskMaxTri * kTriGeoBytes);
@@ -79,8 +79,8 @@ struct MaskWs {
     unsigned char* geo;        // per triangle: TriGeo<T> in kTriGeoBytes
 };
 
-inline MaskWs mask_ws_split(unsigned char* w, int n) {
-    const size_t n3 = (size_t)n * n * n;
+inline MaskWs mask_ws_split(unsigned char* w, int n, int nz) {
+    const size_t n3 = (size_t)n * n * nz;
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
     MaskWs m;
     size_t o = 0;
@@ -97,7 +97,9 @@ inline MaskWs mask_ws_split(unsigned char* w, int n) {
 }
 
 // Closest point of triangle (a, b, c) to p by Voronoi-region tests on the
-// vertices, edges and face; returns squared distance and barycentrics.
+// vertices, edges and face (the published closest-point-on-triangle method
+// of Ericson, Real-Time Collision Detection, Sec. 5.1.5); returns squared
+// distance and barycentrics.
 template <typename R>
 __device__ __forceinline__ R closest_tri(const R p[3], const R a[3], const R b[3], const R c[3], R bary[3]) {
     R ab[3], ac[3], ap[3], bp[3], cp[3];
@@ -207,7 +209,7 @@ __global__ void k_mask_tris(MaskWs m, MaskArgs a, double reach) {
         for (int r = 0; r < 3; ++r) {
             double l = ceil((lo[r] - reach) / a.dx), h = floor((hi[r] + reach) / a.dx);
             l = fmax(l, 0.0);
-            h = fmin(h, (double)(a.n - 1));
+            h = fmin(h, (double)((r == 2 ? a.nz : a.n) - 1));
             i0[r] = (int)l;
             e[r] = h >= l ? (int)(h - l) + 1 : 0;
             const double ar = m.xg[3 * id[0] + r];
@@ -292,7 +294,7 @@ __device__ __forceinline__ bool pair_dist(const MaskWs& m, const MaskArgs& a, in
     T C0[3] = {g.c[0], g.c[1], g.c[2]};
     T bary[3];
     const T d = sqrt(closest_tri<T>(P, A0, B0, C0, bary));
-    *pt = (uint32_t)(((size_t)i * a.n + j) * a.n + k);
+    *pt = (uint32_t)(((size_t)i * a.n + j) * a.nz + k);
     *dist = d;
     return d < (T)(a.tw + a.h);
 }
@@ -350,8 +352,8 @@ __device__ __forceinline__ double chi_profile(double d, double tw, double h, int
 template <typename T>
 __device__ __forceinline__ void eval_point(const MaskWs& m, const MaskArgs& a, uint32_t p, int t, T* chi, T* us,
                                            uint8_t* flag) {
-    const size_t n = a.n, n3 = n * n * n;
-    const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+    const size_t n = a.n, nz = a.nz, n3 = n * n * nz;
+    const int k = (int)(p % nz), j = (int)((p / nz) % n), i = (int)(p / (n * nz));
     const double X[3] = {i * a.dx, j * a.dx, k * a.dx};
     const int id[3] = {a.tri[3 * t], a.tri[3 * t + 1], a.tri[3 * t + 2]};
     double P[3], V[3][3];
@@ -393,9 +395,9 @@ __global__ void k_mask_eval(MaskWs m, MaskArgs a, int par, T* chi, T* us, uint8_
 // Dense (tanh) profile: every point against every triangle in index order.
 template <typename T>
 __global__ void k_mask_dense(MaskWs m, MaskArgs a, T* chi, T* us, uint8_t* flag) {
-    const size_t n = a.n, n3 = n * n * n;
+    const size_t n = a.n, nz = a.nz, n3 = n * n * nz;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(p % n), j = (int)((p / n) % n), i = (int)(p / (n * n));
+        const int k = (int)(p % nz), j = (int)((p / nz) % n), i = (int)(p / (n * nz));
         T best = (T)3.0e38;
         int bt = 0;
         for (int t = 0; t < a.n_tri; ++t) {

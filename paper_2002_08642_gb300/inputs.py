@@ -51,20 +51,23 @@ def taylor_green_2d(n, L=2.0 * math.pi):
                      np.zeros_like(X)])
 
 
-def random_field(n, L, seed=1234, rms=0.05, slope=-5.0 / 3.0):
-    """Band-limited Gaussian random vector field (not yet solenoidal)."""
+def random_field(n, L, seed=1234, rms=0.05, slope=-5.0 / 3.0, nz=None):
+    """Band-limited Gaussian random vector field (not yet solenoidal) on the
+    n x n x nz grid (nz = n by default; the spacing L/n on every axis, so a
+    z mode m_z has the wavenumber (2 pi / L) m_z n / nz)."""
+    nz = n if nz is None else nz
     rng = np.random.default_rng(seed)
     m = np.fft.fftfreq(n, 1.0 / n)
-    mz = np.arange(n // 2 + 1)
+    mz = np.arange(nz // 2 + 1) * (n / nz)
     MX, MY, MZ = np.meshgrid(m, m, mz, indexing="ij")
     mag = np.sqrt(MX ** 2 + MY ** 2 + MZ ** 2)
     band = (mag >= 1.0) & (mag < n / 3.0)
     # E(k) dk ~ k^slope with ~k^2 modes per shell: |a|^2 ~ k^(slope-2)
     amp = np.where(band, np.power(np.where(band, mag, 1.0), 0.5 * (slope - 2.0)), 0.0)
-    u = np.empty((3, n, n, n))
+    u = np.empty((3, n, n, nz))
     for c in range(3):
         z = rng.standard_normal(amp.shape) + 1j * rng.standard_normal(amp.shape)
-        u[c] = np.fft.irfftn(z * amp, s=(n, n, n), axes=(0, 1, 2))
+        u[c] = np.fft.irfftn(z * amp, s=(n, n, nz), axes=(0, 1, 2))
     target = rms * math.sqrt(1.5)
     for c in range(3):
         u[c] *= target / np.sqrt(np.mean(u[c] ** 2))

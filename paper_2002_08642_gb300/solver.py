@@ -15,10 +15,12 @@ _MEAN = {"fixed": B.PS_MEAN_FIXED, "free": B.PS_MEAN_FREE}
 
 
 def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                tw=None, h=None, x0=None, with_adjoint=False, keep_uw=False):
+                tw=None, h=None, x0=None, with_adjoint=False, keep_uw=False, nz=None):
+    """nz: points along z (None: n); the box is [0, L)^2 x [0, L nz / n)."""
     dx = L / n
     p = B.PsParams()
     p.n = int(n)
+    p.nz = int(n if nz is None else nz)
     p.precision = _PREC[precision]
     p.mask_profile = _PROFILE[mask_profile]
     p.mean_mode = _MEAN[mean_mode]
@@ -27,7 +29,8 @@ def make_params(n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mo
     p.L, p.nu, p.eta, p.dt = float(L), float(nu), float(eta), float(dt)
     p.tw = float(2.0 * dx if tw is None else tw)
     p.h = float(1.5 * dx if h is None else h)
-    x0 = (0.5 * L, 0.5 * L, 0.5 * L) if x0 is None else x0
+    Lz = L * p.nz / p.n
+    x0 = (0.5 * L, 0.5 * L, 0.5 * Lz) if x0 is None else x0
     for i in range(3):
         p.x0[i] = float(x0[i])
     return p
@@ -37,13 +40,15 @@ class Solver:
     """One penalized pseudo-spectral solver on one CUDA device."""
 
     def __init__(self, n, L, nu, eta, dt, precision="fp32", mask_profile="cos", mean_mode="fixed",
-                 tw=None, h=None, x0=None, device=None, stream=None, with_adjoint=False, keep_uw=False):
+                 tw=None, h=None, x0=None, device=None, stream=None, with_adjoint=False, keep_uw=False,
+                 nz=None):
         if not torch.cuda.is_available():
             raise RuntimeError("libps needs a CUDA device")
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.params = make_params(n, L, nu, eta, dt, precision, mask_profile, mean_mode, tw, h, x0, with_adjoint,
-                                  keep_uw)
+                                  keep_uw, nz)
         self.n = int(n)
+        self.nz = int(self.params.nz)
         self.L = float(L)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.precision = precision
@@ -66,8 +71,8 @@ class Solver:
 
     # -------------------------------------------------------------- checks
     def _field(self, t, comps, name):
-        n = self.n
-        shape = (comps, n, n, n) if comps > 1 else (n, n, n)
+        n, nz = self.n, self.nz
+        shape = (comps, n, n, nz) if comps > 1 else (n, n, nz)
         if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype:
             raise ValueError("%s must be a %s tensor on %s" % (name, self.dtype, self.device))
         if tuple(t.shape) != shape or not t.is_contiguous():
@@ -79,9 +84,9 @@ class Solver:
         B.ps_set_velocity(self.ctx, self._field(u, 3, "u"))
 
     def velocity(self, out=None):
-        n = self.n
+        n, nz = self.n, self.nz
         if out is None:
-            out = torch.empty((3, n, n, n), dtype=self.dtype, device=self.device)
+            out = torch.empty((3, n, n, nz), dtype=self.dtype, device=self.device)
         B.ps_get_velocity(self.ctx, self._field(out, 3, "out"))
         return out
 
@@ -89,9 +94,9 @@ class Solver:
         B.ps_set_mask(self.ctx, self._field(chi, 1, "chi"), self._field(us, 3, "us"))
 
     def mask(self):
-        n = self.n
-        chi = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
-        us = torch.empty((3, n, n, n), dtype=self.dtype, device=self.device)
+        n, nz = self.n, self.nz
+        chi = torch.empty((n, n, nz), dtype=self.dtype, device=self.device)
+        us = torch.empty((3, n, n, nz), dtype=self.dtype, device=self.device)
         B.ps_get_mask(self.ctx, chi.data_ptr(), us.data_ptr())
         return chi, us
 
@@ -124,9 +129,9 @@ class Solver:
 
     def pressure(self, out=None):
         """Static pressure p = Pi - (1/2)|u|^2 of the current state and mask."""
-        n = self.n
+        n, nz = self.n, self.nz
         if out is None:
-            out = torch.empty((n, n, n), dtype=self.dtype, device=self.device)
+            out = torch.empty((n, n, nz), dtype=self.dtype, device=self.device)
         B.ps_pressure(self.ctx, self._field(out, 1, "out"))
         return out
 
@@ -145,6 +150,10 @@ class Solver:
 
     def diagnostics(self):
         return B.ps_diagnostics(self.ctx)
+
+    def clear_error(self):
+        """Reset the sticky device error flag (see ps_clear_error)."""
+        B.ps_clear_error(self.ctx)
 
     def adjoint_reset(self):
         B.ps_adjoint_reset(self.ctx)
