@@ -561,6 +561,8 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm < 1) nsm = 1;
     cudaError_t e = ops->prepare(nsm, &c->zblocks);
+    kp.nparts = c->zblocks;
+    kp.part_off = 0;
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
         if (!encode_planes(&c->tmA, c->b.A, c->fp64, kp.Kzp, (size_t)n, (size_t)6 * Kk, ops->cy2, ops->br2) ||

@@ -3,6 +3,7 @@
 // function pointers so that the C ABI can dispatch on the runtime grid size.
 #pragma once
 #include "ps_kernels.cuh"
+#include "ps_zstep.cuh"
 
 namespace ps {
 
@@ -84,6 +85,13 @@ template <typename T, int N, int NZ = N> struct Engine {
         static int g = 0;
         return g;
     }
+    // the step's z pass: k_zstep (registers) where it applies, else k_zpass
+    using ZS = ZGeo<T, NZ>;
+    static constexpr bool use_zstep = ZS::ok && PS_ZSTEP != 0 && (N * N) % ZS::LB == 0;
+    static int& zsgrid() {
+        static int g = 0;
+        return g;
+    }
     static int& y2grid() {
         static int g = 0;
         return g;
@@ -137,6 +145,15 @@ template <typename T, int N, int NZ = N> struct Engine {
         const int nb = N * N / GZ::LZ;
         zgrid() = nsm * occ < nb ? nsm * occ : nb;
         *zb = zgrid();
+        if constexpr (use_zstep) {
+            if ((e = attr(k_zstep<T, NZ>, ZS::smem()))) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zstep<T, NZ>, ZS::NT, ZS::smem())))
+                return e;
+            if (occ < 1) occ = 1;
+            const int nbs = N * N / ZS::LB;
+            zsgrid() = nsm * occ < nbs ? nsm * occ : nbs;
+            if (zsgrid() > *zb) *zb = zsgrid();
+        }
         if ((e = attr(k_yinv_tma<T, N>, sm_y2))) return e;
         if ((e = attr(k_yfwd_tma<T, N, GE::CY4>, sm_y4))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yinv_tma<T, N>, thr_y2, sm_y2))) return e;
@@ -186,6 +203,9 @@ template <typename T, int N, int NZ = N> struct Engine {
             k_zpass<T, NZ, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                                      b.flag, b.partial, twz(b.tw), b.err, nullptr,
                                                                      (const T*)b.chi_sp, (C2*)b.B);
+        else if constexpr (use_zstep)
+            k_zstep<T, NZ><<<zsgrid(), ZS::NT, ZS::smem(), s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+                                                               b.flag, b.partial, twz(b.tw), b.err);
         else
             k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                         b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);

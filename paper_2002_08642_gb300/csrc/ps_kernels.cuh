@@ -103,6 +103,7 @@ struct KP {
     int mean_free;
     int xs0, xsn;     // x planes [xs0, xs0 + xsn) handled by the y and z passes
     int part_off;     // first force-partial slot of this z-pass launch
+    int nparts;       // force-partial slots ps_forces sums (>= the z-pass grid; the rest are zeroed)
     double inv_csp;   // 1 / C_sp of the sponge term (used by the sponge variants only)
 };
 
@@ -477,6 +478,10 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         load_tw(tw, twg, GE::tw_n);
     }
     for (int i = threadIdx.x; i < 32 * 12; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
+    // slots of the force partials this launch does not reach stay zero
+    if (!PM && blockIdx.x == 0)
+        for (int i = (int)gridDim.x * 6 + threadIdx.x; i < kp.nparts * 6; i += blockDim.x)
+            partial[(size_t)kp.part_off * 6 + i] = 0.0;
     __syncthreads();
     auto issue = [&](int b, int buf) {  // one thread
         fence_proxy_async();
