@@ -32,6 +32,8 @@ WORKLOADS = {
     "wing384": dict(n=384, L=4.0, nodes=2000, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
     "wing256": dict(n=256, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
     "wing128": dict(n=128, L=4.0, nodes=600, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
+    # the paper's revolving-wing box (Sec. 4.2): 4 x 4 x 2 with N x N x N/2 points
+    "wing768x384": dict(n=768, nz=384, L=4.0, nodes=2000, nu=1.527e-4, eta=1e-3, dt=5e-4, precision="fp32"),
 }
 
 CPU_SAMPLE_N = 48
@@ -55,16 +57,18 @@ def fma_peak(precision, iters, stream_ptr):
         raise RuntimeError("bench_fma_peak failed with status %d" % st)
     return out.value
 
-def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4):
+def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4, nz=None):
     """Bytes each pass must move per step with the 2/3-truncated storage
-    (reads + writes of the kept modes only), keyed by pass name."""
+    (reads + writes of the kept modes only) on the n x n x nz grid, keyed
+    by pass name."""
+    nz = n if nz is None else nz
     mm = (n - 1) // 3
-    K, Kz = 2 * mm + 1, mm + 1
+    K, Kz = 2 * mm + 1, (nz - 1) // 3 + 1
     kk = K * K * Kz
     nk = n * K * Kz
     nn = n * n * Kz
     e = elem_complex
-    mask = flagged_lines * n * 4 * elem_real + n * n  # chi + u_s on flagged lines, flags
+    mask = flagged_lines * nz * 4 * elem_real + n * n  # chi + u_s on flagged lines, flags
     return {
         "x_inverse_curl": (3 * kk + 6 * nk) * e,
         "y_inverse": (6 * nk + 6 * nn) * e,
@@ -72,6 +76,49 @@ def algorithmic_bytes(n, elem_complex, flagged_lines=0, elem_real=4):
         "y_forward": (3 * nn + 3 * nk) * e,
         "x_forward_project_ab2": (3 * nk + 3 * kk + 6 * kk) * e,   # reads N, Q; writes U, Q
     }
+
+
+def adjoint_bytes(n, elem_complex, elem_real):
+    """Algorithmic bytes of one reversed step (ps_adjoint_step, FP32 or
+    FP64 storage), per kernel family; the checkpoint recompute of the
+    forward steps and the rasteriser VJP (band points only) are not counted.
+    State arrays are 3 x K^2 Kz (lam, mu, G, Ub, Wb), z-spectral 3 x n^2 Kz,
+    physical 3 x n^3."""
+    mm = (n - 1) // 3
+    K, Kz = 2 * mm + 1, mm + 1
+    kk, nk, nn = K * K * Kz, n * K * Kz, n * n * Kz
+    e, r_ = elem_complex, elem_real
+    n3 = n ** 3
+    return {
+        "spectral_1": 5 * 3 * kk * e,                                # lam, mu in; G, lam, mu out
+        "inverse_u_omega": (3 * kk + 6 * nk) * e + (6 * nk + 6 * nn) * e + 6 * nn * e + 6 * n3 * r_,
+        "inverse_G": (3 * kk + 3 * nk) * e + (3 * nk + 3 * nn) * e + 3 * nn * e + 3 * n3 * r_,
+        "pointwise": 23 * n3 * r_,                                   # u, w, nbar, chi, u_s in; ubar, wbar, grads out
+        "forward_2x3": 2 * (3 * n3 * r_ + 3 * nn * e + (3 * nn + 3 * nk) * e + (3 * nk + 3 * kk) * e),
+        "spectral_2": 12 * kk * e,                                   # lam, Ub, Wb in; lam out
+    }
+
+
+def host_info():
+    """CPU model, logical cores and RAM of this host (for the CPU baseline)."""
+    import platform
+
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    ram = None
+    try:
+        with open("/proc/meminfo") as f:
+            ram = round(int(f.readline().split()[1]) / 1024 ** 2, 1)
+    except (OSError, ValueError, IndexError):
+        pass
+    return {"cpu_model": model, "arch": platform.machine(), "nproc": os.cpu_count(), "ram_gib": ram}
 
 
 def step_flops(n):
@@ -182,29 +229,86 @@ def measured_traffic(kernel, n):
 
 
 def wing_inputs(cfg, steps):
+    """Revolving-wing node positions, velocities and frames of `steps` steps,
+    hinge at the box centre."""
     from paper_2002_08642_gb300 import inputs
 
+    L = cfg["L"]
+    Lz = L * cfg.get("nz", cfg["n"]) / cfg["n"]
     xw0, tri = inputs.elliptic_wing_mesh(cfg["nodes"])
     amp = inputs.flapping_amplitudes(xw0)
-    seq = [inputs.revolving_wing(k * cfg["dt"], xw0, amp) for k in range(steps)]
+    seq = [inputs.revolving_wing(k * cfg["dt"], xw0, amp, centre=(L / 2, L / 2, Lz / 2)) for k in range(steps)]
     return tri, seq
 
 
-def cpu_oracle_rate(cfg, budget_s=12.0):
-    """The oracle stepping the same workload recipe at CPU_SAMPLE_N^3 for about
-    budget_s seconds: (Mpts*steps/s, steps, n)."""
+def timed_leg(cfg, precision, steps, warmup, dev):
+    """Rasterise + step of a revolving-wing workload on a fresh context:
+    ms per step (CUDA events around `steps` steps after `warmup`), the
+    per-pass times, the flagged z lines and the step's algorithmic bytes."""
+    import torch
+
+    from paper_2002_08642_gb300.solver import Solver
+
+    n, nz, L = cfg["n"], cfg.get("nz", cfg["n"]), cfg["L"]
+    tri, seq = wing_inputs(cfg, warmup + steps)
+    g = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision=precision, device=dev, nz=nz)
+    dt_ = torch.float64 if precision == "fp64" else torch.float32
+    g.set_velocity(torch.zeros((3, n, n, nz), dtype=dt_, device=dev))
+    tri_d = torch.from_numpy(tri).to(dev, torch.int32)
+    xs = [torch.from_numpy(q[0]).to(dev, torch.float64) for q in seq]
+    vs = [torch.from_numpy(q[1]).to(dev, torch.float64) for q in seq]
+    for k in range(warmup):
+        g.set_mask_from_nodes(xs[k], vs[k], tri_d, seq[k][2])
+        g.step(1)
+    torch.cuda.synchronize()
+    flagged = int(g.mask()[0].reshape(n * n, nz).gt(0).any(dim=1).sum().item())
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.timing(True)
+    e0.record(stream)
+    for k in range(warmup, warmup + steps):
+        g.set_mask_from_nodes(xs[k], vs[k], tri_d, seq[k][2])
+        g.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    passes = {k: v[0] / max(v[1], 1) for k, v in g.timing_read().items()}
+    g.timing(False)
+    del g
+    torch.cuda.empty_cache()
+    ab = algorithmic_bytes(n, 8 if precision == "fp32" else 16, flagged, 4 if precision == "fp32" else 8, nz)
+    return ms, passes, flagged, ab
+
+
+def roofline_of(passes, ab, peak, src, ms_step):
+    """Dominant transform pass against the HBM peak, and the whole step."""
+    fft = {k: v for k, v in passes.items() if k in ab}
+    top = max(fft, key=lambda k: fft[k])
+    ach = ab[top] / (fft[top] / 1e3) / 1e9
+    sb = sum(ab.values())
+    return ({"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+             "peak_source": src, "algorithmic_bytes_per_launch": ab[top]},
+            {"algorithmic_bytes_per_step": sb, "achieved_GBs": sb / (ms_step / 1e3) / 1e9,
+             "frac": sb / (ms_step / 1e3) / 1e9 / peak,
+             "passes": {k: {"ms": fft[k], "GBs": ab[k] / (fft[k] / 1e3) / 1e9,
+                            "frac": ab[k] / (fft[k] / 1e3) / 1e9 / peak} for k in fft}})
+
+
+def cpu_oracle_rate(cfg, budget_s=12.0, n=CPU_SAMPLE_N, min_steps=2):
+    """The oracle stepping the same workload recipe at n^3 for about budget_s
+    seconds (at least min_steps steps): (Mpts*steps/s, steps, n)."""
     from oracle import mask as OM
     from oracle import step as S
     from paper_2002_08642_gb300 import inputs
 
-    n, L = CPU_SAMPLE_N, cfg["L"]
+    L = cfg["L"]
     dx = L / n
     o = S.Solver(S.Params(n=n, L=L, nu=cfg["nu"], eta=cfg["eta"], dt=cfg["dt"], x0=(L / 2,) * 3))
     o.set_velocity(inputs.random_field(n, L, seed=1234))
     tri, seq = wing_inputs(cfg, 64)
     t0 = time.perf_counter()
     k = 0
-    while k < 2 or (time.perf_counter() - t0 < budget_s and k < len(seq)):
+    while k < min_steps or (time.perf_counter() - t0 < budget_s and k < len(seq)):
         xw, vw, fr = seq[k]
         chi, us, _, _ = OM.rasterise(n, L, xw, vw, tri, fr, 2 * dx, 1.5 * dx)
         o.set_mask(chi, us)
@@ -236,7 +340,8 @@ def run_reference(args, cfg):
         "config": {"workload": args.workload, "sample_n": CPU_SAMPLE_N},
         "cpu_baseline": {"value": value, "unit": "Mpts*steps/s", "cores": 1, "kind": "oracle",
                          "sample": "FP64 numpy oracle stepping the same revolving-wing recipe at %d^3 "
-                                   "(rasterise + step), ~5 s per bench step" % CPU_SAMPLE_N},
+                                   "(rasterise + step), ~5 s per bench step" % CPU_SAMPLE_N,
+                         "host": host_info()},
         "e2e": {"value": value, "unit": "Mpts*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -261,11 +366,12 @@ def run_ours(args, cfg):
     pbuild.build()
 
     n, L = cfg["n"], cfg["L"]
+    nz = cfg.get("nz", n)
     total = args.warmup + args.steps
     tri, seq = wing_inputs(cfg, total + args.steps)
-    g = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision=cfg["precision"], device=dev)
+    g = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision=cfg["precision"], device=dev, nz=nz)
     # the revolving-wing configurations start from rest (u^0 = 0)
-    u = torch.zeros((3, n, n, n), dtype=g.dtype, device=dev)
+    u = torch.zeros((3, n, n, nz), dtype=g.dtype, device=dev)
     g.set_velocity(u)
     del u
     tri_d = torch.from_numpy(tri).to(dev, torch.int32)
@@ -280,7 +386,7 @@ def run_ours(args, cfg):
     for k in range(args.warmup):
         one(k)
     torch.cuda.synchronize()
-    flagged = int(g.mask()[0].reshape(n * n, n).gt(0).any(dim=1).sum().item())
+    flagged = int(g.mask()[0].reshape(n * n, nz).gt(0).any(dim=1).sum().item())
 
     def barrier():
         if world > 1:
@@ -306,7 +412,8 @@ def run_ours(args, cfg):
     clk = clocks.stop()
     F, M = g.forces()
     ms = max_over_ranks(ms, world)
-    value = n ** 3 * args.steps * world / (ms / 1e3) / 1e6
+    npts = n * n * nz
+    value = npts * args.steps * world / (ms / 1e3) / 1e6
 
     # ---- end to end through the public API with host buffers
     xw_h = [torch.from_numpy(s[0]).pin_memory() for s in seq[total:total + args.steps]]
@@ -325,13 +432,13 @@ def run_ours(args, cfg):
         g.forces()  # device -> host read of F, M (synchronises)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = n ** 3 * args.steps * world / e2e_s / 1e6
+    e2e = npts * args.steps * world / e2e_s / 1e6
     h2d = 2 * xw_h[0].numel() * 8
     d2h = 6 * 8
 
     # ---- roofline of the dominant pass
     ab = algorithmic_bytes(n, 8 if cfg["precision"] == "fp32" else 16, flagged,
-                           4 if cfg["precision"] == "fp32" else 8)
+                           4 if cfg["precision"] == "fp32" else 8, nz)
     fft_passes = {k: v for k, v in passes.items() if k in ab}
     top = max(fft_passes, key=lambda k: fft_passes[k][0])
     tms, tl = fft_passes[top]
@@ -372,7 +479,7 @@ def run_ours(args, cfg):
         out["clocks"] = clk
     # pressure of the stepped state and its loads on the nodes (the coupling
     # step that follows every fluid step), same workload
-    pfield = torch.empty((n, n, n), dtype=g.dtype, device=dev)
+    pfield = torch.empty((n, n, nz), dtype=g.dtype, device=dev)
     for _ in range(2):
         g.pressure(pfield)
         g.pressure_loads(pfield, xw_d[0], tri_d, frames[0])
@@ -385,12 +492,13 @@ def run_ours(args, cfg):
     e1.record(stream)
     torch.cuda.synchronize()
     msp = e0.elapsed_time(e1) / kp_
-    out["pressure_loads"] = {"value": n ** 3 / (msp / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_call": msp,
+    out["pressure_loads"] = {"value": npts / (msp / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_call": msp,
                              "calls": kp_, "nodes": int(xw_d[0].shape[0]),
                              "note": "static pressure of the state (passes 1-4, Pi_hat, one inverse field) "
                                      "+ delta interpolation and p A/3 loads on the nodes"}
     del pfield
-    if args.fsi and world == 1:
+    cubic = nz == n
+    if args.fsi and world == 1 and cubic:
         # staggered FSI step (fluid step, pressure, loads, host mass-spring
         # step, rasterised mask of the new nodes) with an 833-node network
         from paper_2002_08642_gb300.fsi import FSI
@@ -426,7 +534,7 @@ def run_ours(args, cfg):
         del cpl, msn
     del g
     torch.cuda.empty_cache()
-    if args.fp64 and world == 1:
+    if args.fp64 and world == 1 and cubic:
         g64 = Solver(n, L, cfg["nu"], cfg["eta"], cfg["dt"], precision="fp64", device=dev)
         g64.set_velocity(torch.zeros((3, n, n, n), dtype=torch.float64, device=dev))
         k64 = max(2, args.steps // 4)
@@ -453,39 +561,34 @@ def run_ours(args, cfg):
         del g64
         torch.cuda.empty_cache()
     if args.small and world == 1 and n != 256:
-        # the 256^3 revolving-wing configuration (600 nodes), FP32 and FP64 steps
+        # the 256^3 revolving-wing configuration (600 nodes), FP32 and FP64
+        # steps, with the per-pass breakdown and the step's HBM roofline
         c2 = WORKLOADS["wing256"]
-        tri2, seq2 = wing_inputs(c2, 24)
-        tri2_d = torch.from_numpy(tri2).to(dev, torch.int32)
-        res = {}
-        for prec, dt_, ks in (("fp32", torch.float32, 20), ("fp64", torch.float64, 8)):
-            g2 = Solver(c2["n"], c2["L"], c2["nu"], c2["eta"], c2["dt"], precision=prec, device=dev)
-            g2.set_velocity(torch.zeros((3, c2["n"], c2["n"], c2["n"]), dtype=dt_, device=dev))
-            xs = [torch.from_numpy(q[0]).to(dev, torch.float64) for q in seq2]
-            vs = [torch.from_numpy(q[1]).to(dev, torch.float64) for q in seq2]
-            for k in range(3):
-                g2.set_mask_from_nodes(xs[k], vs[k], tri2_d, seq2[k][2])
-                g2.step(1)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for k in range(3, 3 + ks):
-                g2.set_mask_from_nodes(xs[k], vs[k], tri2_d, seq2[k][2])
-                g2.step(1)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            m2 = e0.elapsed_time(e1) / ks
-            res[prec] = (c2["n"] ** 3 / (m2 / 1e3) / 1e6, m2, ks)
-            del g2
-            torch.cuda.empty_cache()
-        out["wing256_step"] = {"value": res["fp32"][0], "unit": "Mpts*steps/s", "ms_per_step": res["fp32"][1],
-                               "steps": res["fp32"][2], "fp64_value": res["fp64"][0],
-                               "fp64_ms_per_step": res["fp64"][1], "fp64_steps": res["fp64"][2],
-                               "fp32_speedup": res["fp32"][0] / res["fp64"][0],
+        ms32, pass32, fl32, ab32 = timed_leg(c2, "fp32", 20, 3, dev)
+        ms64_, _, _, _ = timed_leg(c2, "fp64", 8, 3, dev)
+        pk, src_ = peaks()
+        top2, step2 = roofline_of(pass32, ab32, pk, src_, ms32)
+        v32, v64_ = c2["n"] ** 3 / (ms32 / 1e3) / 1e6, c2["n"] ** 3 / (ms64_ / 1e3) / 1e6
+        out["wing256_step"] = {"value": v32, "unit": "Mpts*steps/s", "ms_per_step": ms32, "steps": 20,
+                               "fp64_value": v64_, "fp64_ms_per_step": ms64_, "fp64_steps": 8,
+                               "fp32_speedup": v32 / v64_, "passes_ms": pass32, "roofline": top2,
+                               "step_roofline": step2, "flagged_lines": fl32,
                                "note": "256^3 revolving wing, 600 nodes, rasterise + step, inputs resident"}
+    if args.aniso and world == 1 and cubic:
+        # the paper's 4 x 4 x 2 box at 768 x 768 x 384 (Sec. 4.2 grids), FP32
+        ca = WORKLOADS["wing768x384"]
+        msa_, passa, fla, aba = timed_leg(ca, "fp32", 10, 3, dev)
+        pk, src_ = peaks()
+        topa, stepa = roofline_of(passa, aba, pk, src_, msa_)
+        na3 = ca["n"] * ca["n"] * ca["nz"]
+        out["aniso_step"] = {"value": na3 / (msa_ / 1e3) / 1e6, "unit": "Mpts*steps/s", "ms_per_step": msa_,
+                             "steps": 10, "grid": [ca["n"], ca["n"], ca["nz"]], "box": [4.0, 4.0, 2.0],
+                             "passes_ms": passa, "roofline": topa, "step_roofline": stepa,
+                             "note": "revolving wing, 2000 nodes, rasterise + step, FP32, inputs resident"}
     if args.adjoint and world == 1:
         # adjoint step throughput at 512^3 (FP32): one reversed step per call,
         # on the state and mask reached by a few forward steps
-        na = 512
+        na = args.adjoint_n
         ga = Solver(na, L, cfg["nu"], cfg["eta"], cfg["dt"], precision="fp32", device=dev, with_adjoint=True)
         ga.set_velocity(torch.zeros((3, na, na, na), dtype=torch.float32, device=dev))
         ga.set_mask_from_nodes(xw_d[0], vw_d[0], tri_d, frames[0])
@@ -506,16 +609,31 @@ def run_ours(args, cfg):
         e1.record(stream)
         torch.cuda.synchronize()
         msa = e0.elapsed_time(e1)
+        adj_b = adjoint_bytes(na, 8, 4)
+        pk, src_ = peaks()
+        adj_tot = sum(adj_b.values())
         out["adjoint_step"] = {"value": na ** 3 * ka / (msa / 1e3) / 1e6, "unit": "Mpts*steps/s", "n": na,
                                "precision": "fp32", "steps": ka, "ms_per_step": msa / ka,
-                               "note": "reversed step + rasteriser VJP, excluding the checkpoint recompute"}
+                               "roofline": {"bound": "hbm", "algorithmic_bytes_per_step": adj_tot,
+                                            "bytes_by_kernel_family": adj_b,
+                                            "achieved": adj_tot / (msa / ka / 1e3) / 1e9, "peak": pk,
+                                            "unit": "GB/s", "frac": adj_tot / (msa / ka / 1e3) / 1e9 / pk,
+                                            "peak_source": src_},
+                               "note": "reversed step + rasteriser VJP, excluding the checkpoint recompute "
+                                       "(the byte model leaves out the VJP, which touches the band points only)"}
         del ga
         torch.cuda.empty_cache()
     if rank == 0 and args.cpu_baseline:
         r, k, cn = cpu_oracle_rate(cfg)
+        # the configurations' own small sizes: median of three runs each
+        by_n = {}
+        for nn_, steps_ in ((32, 4), (128, 1)):
+            rr = [cpu_oracle_rate(cfg, budget_s=0.0, n=nn_, min_steps=steps_)[0] for _ in range(3)]
+            by_n[str(nn_)] = {"value": statistics.median(rr), "runs": rr, "steps_per_run": steps_}
         out["cpu_baseline"] = {"value": r, "unit": "Mpts*steps/s", "cores": 1, "kind": "oracle",
                                "sample": "FP64 numpy oracle, same revolving-wing recipe at %d^3, "
-                                         "%d steps (rasterise + step), single-threaded numpy" % (cn, k)}
+                                         "%d steps (rasterise + step), single-threaded numpy" % (cn, k),
+                               "by_n": by_n, "host": host_info()}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -534,6 +652,8 @@ def main():
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-256", dest="small", action="store_false")
     ap.add_argument("--no-fsi", dest="fsi", action="store_false")
+    ap.add_argument("--no-aniso", dest="aniso", action="store_false")
+    ap.add_argument("--adjoint-n", type=int, default=512, help="grid of the adjoint-step leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

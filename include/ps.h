@@ -169,6 +169,37 @@ ps_status ps_step(ps_ctx* ctx, int32_t nsteps);
  * the last step taken (Sec. 4.2.2 defines lift and drag from this force).
  * Host outputs; synchronises the stream. */
 ps_status ps_forces(ps_ctx* ctx, double F[3], double M[3]);
+/* Spectral array sizes of the context: K kept x/y modes (x/y index c <->
+ * mode c if c <= (n-1)/3, else c - K), Kz kept z modes, Kzp the padded kz
+ * columns of every spectral array. Host outputs. */
+ps_status ps_grid_info(const ps_ctx* ctx, int32_t* K, int32_t* Kz, int32_t* Kzp);
+
+/* Slab decomposition of the step (the paper's solver runs MPI slabs,
+ * Sec. 4.1; here one context per slab, on one or several GPUs). A slab
+ * context runs its share of each pass:
+ *   phase 0  x-inverse with the curl on its kept ky rows [ky0, ky1)
+ *            (writes the x-pass array A, fields 0..5, those ky rows, all x);
+ *   phase 1  y-inverse, z pass (n, forces) and y-forward on its x-planes
+ *            [x0, x1) (reads A fields 0..5 at those x-planes, all ky rows;
+ *            writes A fields 0..2 at those x-planes, all ky rows);
+ *   phase 2  x-forward, projection and the integrating-factor AB2 update on
+ *            its ky rows (reads A fields 0..2 at those ky rows, all x).
+ * Between phases 0 and 1 every slab needs the other slabs' A rows for its
+ * x-planes, between 1 and 2 their x-planes for its ky rows (the two
+ * all-to-all exchanges of the sharded step); the caller moves those blocks
+ * (ps_slab_buffer gives A). ps_forces of a slab context is its x-planes'
+ * share of F and M; the step's force is the sum over the slabs. The state
+ * (U, H) of a slab context is valid on its ky rows only; its mask is used
+ * on its x-planes only, and ps_set_mask_from_nodes rasterises only them.
+ * ps_slab_set: PS_EINVAL for empty or out-of-range bounds, or x-plane bounds
+ * whose product with n is not a multiple of the z pass's lines per batch.
+ * ps_slab_phase: asynchronous; phase 2 counts the step (the first is the
+ * Euler start). ps_slab_buffer: A, 6 x [K][n][Kzp] complex in the context
+ * precision, [field][ky][x][kz], owned by the context's workspace. */
+ps_status ps_slab_set(ps_ctx* ctx, int32_t x0, int32_t x1, int32_t ky0, int32_t ky1);
+ps_status ps_slab_phase(ps_ctx* ctx, int32_t phase);
+ps_status ps_slab_buffer(ps_ctx* ctx, void** a_dev, size_t* bytes);
+
 /* Device error flag. Every wait of a kernel on its asynchronous copies has
  * an iteration cap; a wait that gives up sets the context's device error
  * flag, lets the copies it started land, and ends the kernel early, so the

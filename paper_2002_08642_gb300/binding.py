@@ -59,6 +59,10 @@ _SIGS = {
     "ps_forces": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_diagnostics": (c_int32, [c_void_p, _P(c_double), _P(c_double)]),
     "ps_clear_error": (c_int32, [c_void_p]),
+    "ps_grid_info": (c_int32, [c_void_p, _P(c_int32), _P(c_int32), _P(c_int32)]),
+    "ps_slab_set": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32]),
+    "ps_slab_phase": (c_int32, [c_void_p, c_int32]),
+    "ps_slab_buffer": (c_int32, [c_void_p, _P(c_void_p), _P(c_size_t)]),
     "ps_debug_wait_timeout": (c_int32, [c_void_p, c_int32]),
     "ps_pressure": (c_int32, [c_void_p, c_void_p]),
     "ps_set_sponge": (c_int32, [c_void_p, c_void_p, c_double]),
@@ -209,6 +213,26 @@ def ps_diagnostics(ctx):
     st = lib().ps_diagnostics(ctx, ctypes.byref(e), ctypes.byref(d))
     check(st, ctx)
     return e.value, d.value
+
+
+def ps_grid_info(ctx):
+    K, Kz, Kzp = c_int32(0), c_int32(0), c_int32(0)
+    check(lib().ps_grid_info(ctx, ctypes.byref(K), ctypes.byref(Kz), ctypes.byref(Kzp)), ctx)
+    return K.value, Kz.value, Kzp.value
+
+
+def ps_slab_set(ctx, x0, x1, ky0, ky1):
+    check(lib().ps_slab_set(ctx, int(x0), int(x1), int(ky0), int(ky1)), ctx)
+
+
+def ps_slab_phase(ctx, phase):
+    check(lib().ps_slab_phase(ctx, int(phase)), ctx)
+
+
+def ps_slab_buffer(ctx):
+    ptr, nb = c_void_p(0), c_size_t(0)
+    check(lib().ps_slab_buffer(ctx, ctypes.byref(ptr), ctypes.byref(nb)), ctx)
+    return ptr.value, nb.value
 
 
 def ps_clear_error(ctx):

@@ -54,6 +54,9 @@ struct ps_ctx {
     bool has_last_mask;
     int nstep;
     int has_velocity;
+    // slab of the sharded step (ps_slab_set): x-planes and kept ky rows
+    bool slab;
+    int slab_x0, slab_x1, slab_ky0, slab_ky1;
     // per-pass timing: a ring of events, kTimingRing steps deep
     bool timing;
     std::vector<cudaEvent_t> tev_step;   // kTimingRing x kEvPerStep
@@ -561,8 +564,11 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (nsm < 1) nsm = 1;
     cudaError_t e = ops->prepare(nsm, &c->zblocks);
-    kp.nparts = c->zblocks;
     kp.part_off = 0;
+    kp.xs0 = 0;
+    kp.xsn = n;
+    kp.ky0 = 0;
+    kp.kyn = kp.K;
     if (e == cudaSuccess) {
         const int Kk = 2 * mm + 1;
         if (!encode_planes(&c->tmA, c->b.A, c->fp64, kp.Kzp, (size_t)n, (size_t)6 * Kk, ops->cy2, ops->br2) ||
@@ -685,6 +691,8 @@ ps_status ps_set_mask_from_nodes(ps_ctx* c, const double* xw, const double* vw, 
     MaskArgs a;
     a.n = c->p.n;
     a.nz = c->p.nz;
+    a.x_lo = c->slab ? c->slab_x0 : 0;
+    a.x_hi = c->slab ? c->slab_x1 : c->p.n;
     a.dx = c->kp.dx;
     a.tw = c->p.tw;
     a.h = c->p.h;
@@ -807,6 +815,56 @@ ps_status ps_forces(ps_ctx* c, double F[3], double M[3]) {
     if (s != PS_OK) return s;
     if (derr) return fail(c, PS_ECUDA, "a device-side copy wait gave up (results of the affected steps are invalid)");
     for (int i = 0; i < 3; ++i) { F[i] = h[i]; M[i] = h[3 + i]; }
+    return PS_OK;
+}
+
+ps_status ps_grid_info(const ps_ctx* c, int32_t* K, int32_t* Kz, int32_t* Kzp) {
+    if (!c || !K || !Kz || !Kzp) return PS_EINVAL;
+    *K = c->kp.K;
+    *Kz = c->kp.Kz;
+    *Kzp = c->kp.Kzp;
+    return PS_OK;
+}
+
+ps_status ps_slab_set(ps_ctx* c, int32_t x0, int32_t x1, int32_t ky0, int32_t ky1) {
+    if (!c) return PS_EINVAL;
+    const int n = c->p.n, K = c->kp.K, za = c->ops->zalign;
+    if (x0 < 0 || x1 > n || x0 >= x1 || ky0 < 0 || ky1 > K || ky0 >= ky1)
+        return fail(c, PS_EINVAL, "ps_slab_set: empty or out-of-range slab");
+    if (((long)x0 * n) % za != 0 || ((long)x1 * n) % za != 0)
+        return fail(c, PS_EINVAL, "ps_slab_set: x-plane bounds times n must be multiples of " + std::to_string(za));
+    c->slab = true;
+    c->slab_x0 = x0;
+    c->slab_x1 = x1;
+    c->slab_ky0 = ky0;
+    c->slab_ky1 = ky1;
+    c->uw_valid = false;
+    return PS_OK;
+}
+
+ps_status ps_slab_phase(ps_ctx* c, int32_t phase) {
+    if (!c) return PS_EINVAL;
+    if (!c->slab) return fail(c, PS_ESTATE, "ps_slab_phase: no slab set (ps_slab_set)");
+    if (phase < 0 || phase > 2) return fail(c, PS_EINVAL, "ps_slab_phase: phase must be 0, 1 or 2");
+    if (!c->has_velocity) return fail(c, PS_ESTATE, "ps_slab_phase: no velocity set");
+    DeviceGuard dg(c->device);
+    c->uw_valid = false;
+    KP k = c->kp;
+    k.xs0 = c->slab_x0;
+    k.xsn = c->slab_x1 - c->slab_x0;
+    k.ky0 = c->slab_ky0;
+    k.kyn = c->slab_ky1 - c->slab_ky0;
+    k.part_off = 0;
+    cudaError_t e = c->ops->slab_phase(k, c->b, phase, c->nstep == 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ps_slab_phase");
+    if (phase == 2) c->nstep++;
+    return PS_OK;
+}
+
+ps_status ps_slab_buffer(ps_ctx* c, void** a_dev, size_t* bytes) {
+    if (!c || !a_dev || !bytes) return PS_EINVAL;
+    *a_dev = c->b.A;
+    *bytes = (size_t)6 * c->kp.K * c->p.n * c->kp.Kzp * 2 * c->elem;
     return PS_OK;
 }
 

@@ -3,7 +3,6 @@
 // function pointers so that the C ABI can dispatch on the runtime grid size.
 #pragma once
 #include "ps_kernels.cuh"
-#include "ps_zstep.cuh"
 
 namespace ps {
 
@@ -55,6 +54,12 @@ struct Ops {
     cudaError_t (*inv_g)(const KP&, const Bufs&, void* phys, cudaStream_t);
     // static pressure of the state in U with the current mask (n^3 real)
     cudaError_t (*pressure)(const KP&, const Bufs&, void* p, int resume, cudaStream_t);
+    // one phase of the step on a slab (kp.xs0/xsn x-planes, kp.ky0/kyn ky
+    // rows): 0 x-inverse + curl on the ky rows; 1 y-inverse, z pass and
+    // y-forward on the x-planes; 2 x-forward, projection and update on the
+    // ky rows. The x-planes of a slab start and end at multiples of zalign/n.
+    cudaError_t (*slab_phase)(const KP&, const Bufs&, int phase, int first, cudaStream_t);
+    int zalign;   // z lines per z-pass batch (slab boundaries x n must be multiples)
 };
 
 // N x N x NZ grid: the x and y passes are the kernels of length-N lines,
@@ -64,6 +69,7 @@ template <typename T, int N, int NZ = N> struct Engine {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     using GZ = Geo<T, NZ>;
+    static constexpr int KZ_ = GZ::KZP;   // kz columns (compile-time in the x/y passes)
     static constexpr size_t tw_bytes = (size_t)GE::tw_n * sizeof(C2);
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
@@ -85,13 +91,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         static int g = 0;
         return g;
     }
-    // the step's z pass: k_zstep (registers) where it applies, else k_zpass
-    using ZS = ZGeo<T, NZ>;
-    static constexpr bool use_zstep = ZS::ok && PS_ZSTEP != 0 && (N * N) % ZS::LB == 0;
-    static int& zsgrid() {
-        static int g = 0;
-        return g;
-    }
+
     static int& y2grid() {
         static int g = 0;
         return g;
@@ -145,38 +145,30 @@ template <typename T, int N, int NZ = N> struct Engine {
         const int nb = N * N / GZ::LZ;
         zgrid() = nsm * occ < nb ? nsm * occ : nb;
         *zb = zgrid();
-        if constexpr (use_zstep) {
-            if ((e = attr(k_zstep<T, NZ>, ZS::smem()))) return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zstep<T, NZ>, ZS::NT, ZS::smem())))
-                return e;
-            if (occ < 1) occ = 1;
-            const int nbs = N * N / ZS::LB;
-            zsgrid() = nsm * occ < nbs ? nsm * occ : nbs;
-            if (zsgrid() > *zb) *zb = zsgrid();
-        }
-        if ((e = attr(k_yinv_tma<T, N>, sm_y2))) return e;
-        if ((e = attr(k_yfwd_tma<T, N, GE::CY4>, sm_y4))) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yinv_tma<T, N>, thr_y2, sm_y2))) return e;
+
+        if ((e = attr(k_yinv_tma<T, N, 6, KZ_>, sm_y2))) return e;
+        if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 3, KZ_>, sm_y4))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yinv_tma<T, N, 6, KZ_>, thr_y2, sm_y2))) return e;
         y2grid() = nsm * (occ < 1 ? 1 : occ);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N, GE::CY4>, thr_y4, sm_y4))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_yfwd_tma<T, N, GE::CY4, 3, KZ_>, thr_y4, sm_y4))) return e;
         y4grid() = nsm * (occ < 1 ? 1 : occ);
-        if ((e = attr(k_xinv_tma<T, N>, sm_x1))) return e;
-        if ((e = attr(k_xinv_tma<T, N, 3>, sm_x1))) return e;
-        if ((e = attr(k_yinv_tma<T, N, 3>, sm_y2))) return e;
-        if ((e = attr(k_yinv_tma<T, N, 1>, sm_y2))) return e;
-        if ((e = attr(k_xfwd_tma<T, N, 0>, sm_x5t))) return e;
-        if ((e = attr(k_xfwd_tma<T, N, 1>, sm_x5t))) return e;
-        if ((e = attr(k_xfwd_tma<T, N, 2>, sm_x5t))) return e;
-        if ((e = attr(k_xfwd_tma<T, N, 3>, sm_x5t))) return e;
-        if ((e = attr(k_xfwd_tma<T, N, 0, true>, sm_x5s))) return e;
+        if ((e = attr(k_xinv_tma<T, N, 6, KZ_>, sm_x1))) return e;
+        if ((e = attr(k_xinv_tma<T, N, 3, KZ_>, sm_x1))) return e;
+        if ((e = attr(k_yinv_tma<T, N, 3, KZ_>, sm_y2))) return e;
+        if ((e = attr(k_yinv_tma<T, N, 1, KZ_>, sm_y2))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 0, false, KZ_>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 1, false, KZ_>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 2, false, KZ_>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 3, false, KZ_>, sm_x5t))) return e;
+        if ((e = attr(k_xfwd_tma<T, N, 0, true, KZ_>, sm_x5s))) return e;
         if ((e = attr(k_zpass<T, NZ, false, true>, sm_zp))) return e;
-        if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 6>, sm_y4))) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, true>, thr_x5, sm_x5s)))
+        if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 6, KZ_>, sm_y4))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, true, KZ_>, thr_x5, sm_x5s)))
             return e;
         x5sgrid() = nsm * (occ < 1 ? 1 : occ);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N>, thr_x1, sm_x1))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N, 6, KZ_>, thr_x1, sm_x1))) return e;
         x1grid() = nsm * (occ < 1 ? 1 : occ);
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0>, thr_x5, sm_x5t))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, false, KZ_>, thr_x5, sm_x5t))) return e;
         x5grid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
     }
@@ -195,30 +187,27 @@ template <typename T, int N, int NZ = N> struct Engine {
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         const bool sp = b.chi_sp != nullptr;   // sponge term: six-field z/y-forward variants
         if (ev) cudaEventRecord(ev[0], s);
-        if (!resume) k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
+        if (!resume) k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
         if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
-        if (!resume) k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        if (!resume) k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
         if (sp)
             k_zpass<T, NZ, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                                      b.flag, b.partial, twz(b.tw), b.err, nullptr,
                                                                      (const T*)b.chi_sp, (C2*)b.B);
-        else if constexpr (use_zstep)
-            k_zstep<T, NZ><<<zsgrid(), ZS::NT, ZS::smem(), s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
-                                                               b.flag, b.partial, twz(b.tw), b.err);
         else
             k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                         b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);
         if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
-        if (sp) k_yfwd_tma<T, N, GE::CY4, 6><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
-        else k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        if (sp) k_yfwd_tma<T, N, GE::CY4, 6, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        else k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
         if (ev) { cudaEventRecord(ev[7], s); cudaEventRecord(ev[8], s); }
         if (sp)
-            k_xfwd_tma<T, N, 0, true><<<x5sgrid(), thr_x5, sm_x5s, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
+            k_xfwd_tma<T, N, 0, true, KZ_><<<x5sgrid(), thr_x5, sm_x5s, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
                                                                        (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez,
                                                                        first, tw, b.err);
         else
-            k_xfwd_tma<T, N, 0><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
+            k_xfwd_tma<T, N, 0, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
                                                                 (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez, first, tw,
                                                                 b.err);
         if (ev) cudaEventRecord(ev[9], s);
@@ -229,7 +218,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, twz(b.tw));
         k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
-        k_xfwd_tma<T, N, 1><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
+        k_xfwd_tma<T, N, 1, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         return cudaGetLastError();
     }
@@ -255,8 +244,8 @@ template <typename T, int N, int NZ = N> struct Engine {
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const T*)phys, (C2*)b.B, twz(b.tw));
-        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
-        k_xfwd_tma<T, N, 2><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, (C2*)spec, nullptr,
+        k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
+        k_xfwd_tma<T, N, 2, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, (C2*)spec, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         return cudaGetLastError();
     }
@@ -267,8 +256,8 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        k_xinv_tma<T, N, 3><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmG, k1, (C2*)b.A, tw, b.err);
-        k_yinv_tma<T, N, 3><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        k_xinv_tma<T, N, 3, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmG, k1, (C2*)b.A, tw, b.err);
+        k_yinv_tma<T, N, 3, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)phys, twz(b.tw));
         return cudaGetLastError();
     }
@@ -287,19 +276,19 @@ template <typename T, int N, int NZ = N> struct Engine {
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         if (!resume) {
-            k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
-            k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+            k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
+            k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         }
         C2* nout = b.N3 ? (C2*)b.N3 : (C2*)b.B;
         k_zpass<T, NZ, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                           b.partial, twz(b.tw), b.err, (T*)p, nullptr, nout);
-        k_yfwd_tma<T, N, GE::CY4><<<y4grid(), thr_y4, sm_y4, s>>>(b.N3 ? *b.tmN : *b.tmB, k1, (C2*)b.A, tw,
+        k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(b.N3 ? *b.tmN : *b.tmB, k1, (C2*)b.A, tw,
                                                                   b.err);
         C2* pih = (C2*)b.A + (size_t)3 * N * GE::K * kp.Kzp;
-        k_xfwd_tma<T, N, 3><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
+        k_xfwd_tma<T, N, 3, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, pih, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
-        k_yinv_tma<T, N, 1><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
+        k_yinv_tma<T, N, 1, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
         k_zinv_phys<T, NZ, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw));
         return cudaGetLastError();
     }
@@ -310,11 +299,28 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        k_xinv_tma<T, N><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
-        k_yinv_tma<T, N><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
+        k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
+        k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         const size_t BS = (size_t)N * N * k1.Kzp;
         k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, twz(b.tw));
         k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, twz(b.tw));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t slab_phase(const KP& kp, const Bufs& b, int phase, int first, cudaStream_t s) {
+        const C2* tw = (const C2*)b.tw;
+        if (phase == 0) {
+            k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
+        } else if (phase == 1) {
+            k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, kp, (C2*)b.B, tw, b.err);
+            k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+                                                        b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);
+            k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, kp, (C2*)b.A, tw, b.err);
+        } else {
+            k_xfwd_tma<T, N, 0, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U,
+                                                                (C2*)b.H, (const T*)b.Ex, (const T*)b.Ez, first, tw,
+                                                                b.err);
+        }
         return cudaGetLastError();
     }
 
@@ -333,6 +339,8 @@ template <typename T, int N, int NZ = N> struct Engine {
         o.inv_uw = &inv_uw;
         o.inv_g = &inv_g;
         o.pressure = &pressure;
+        o.slab_phase = &slab_phase;
+        o.zalign = GZ::LZ;
         return o;
     }
 };

@@ -230,11 +230,7 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     struct NoHook {
         __device__ __forceinline__ void operator()() const {}
     };
-    // REGS: the first stage's input t of this thread's single butterfly
-    // (position g + t G) comes from load(t), t a compile-time index after
-    // unrolling, so the caller can keep the inputs in registers.
-    template <int s, bool FROM_TILE, bool BU = false, bool REGS = false, class Addr, class Load, class Store,
-              class Hook = NoHook>
+    template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store, class Hook = NoHook>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
                                                  const Load& load, const Store& store, bool on, unsigned lanes,
                                                  const Hook& hook = Hook()) {
@@ -252,7 +248,6 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
             for (int t = 0; t < r; ++t) {
                 C x;
                 if constexpr (from_tile) x = tile[addr(j + t * NBF)];
-                else if constexpr (REGS) x = load(t);
                 else x = load(j + t * NBF);
                 if constexpr (Ls > 1) {
                     if (t > 0) {
@@ -318,7 +313,7 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
         }
         if constexpr (!last) sync(lanes);
         if constexpr (s == 0 && !last) hook();
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU, REGS>(tile, tw, addr, g, load, store, on, lanes, hook);
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on, lanes, hook);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
@@ -339,34 +334,6 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     static __device__ __forceinline__ void run_bu(C* tile, const C* tw, const Addr& addr, int g,
                                                   const Load& load, const Store& store) {
         stage<0, FROM_TILE, true>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
-    }
-    // Position set of the last stage vs the first: thread g's last-stage
-    // outputs (slot b RL + u at position g + G b + LsL u) are exactly the
-    // first-stage inputs it needs for a transform of the same length
-    // (input t at position g + G t). slot_of(t) is that slot, so the output
-    // registers of one transform can feed the next (run_regs_bu).
-    static constexpr int LsL = ls_at(N, S - 1);
-    static __host__ __device__ constexpr int slot_of(int t) {
-        return S == 1 ? t : (t % (LsL / G)) * RL + t / (LsL / G);
-    }
-    // First stage from registers (load(t), see REGS), last stage to
-    // store(slot, position, value).
-    template <class Addr, class Load, class Store>
-    static __device__ __forceinline__ void run_regs_bu(C* tile, const C* tw, const Addr& addr, int g,
-                                                       const Load& load, const Store& store) {
-        static_assert(LsL % G == 0 || S == 1, "last-stage butterflies must split evenly over the threads");
-        stage<0, false, true, true>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
-    }
-    // Same, for the threads with on == true (warp-synchronous lines only:
-    // the others leave at once; on must be the same for all G threads).
-    template <class Addr, class Load, class Store>
-    static __device__ __forceinline__ void run_regs_bu_masked(C* tile, const C* tw, const Addr& addr, int g,
-                                                              const Load& load, const Store& store, bool on) {
-        static_assert(WS, "masked register transforms need warp-synchronous lines");
-        static_assert(LsL % G == 0 || S == 1, "last-stage butterflies must split evenly over the threads");
-        const unsigned lanes = __ballot_sync(warp_lanes(), on);
-        if (!on) return;
-        stage<0, false, true, true>(tile, tw, addr, g, load, store, true, lanes);
     }
     // Same, for the threads with on == true. Block barriers: the others
     // still take part in them. Warp barriers (WS): the others leave at once

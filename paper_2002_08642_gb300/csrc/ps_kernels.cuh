@@ -102,8 +102,8 @@ struct KP {
     double x0[3];
     int mean_free;
     int xs0, xsn;     // x planes [xs0, xs0 + xsn) handled by the y and z passes
+    int ky0, kyn;     // kept ky rows [ky0, ky0 + kyn) handled by the TMA x passes (slab decomposition)
     int part_off;     // first force-partial slot of this z-pass launch
-    int nparts;       // force-partial slots ps_forces sums (>= the z-pass grid; the rest are zeroed)
     double inv_csp;   // 1 / C_sp of the sponge term (used by the sponge variants only)
 };
 
@@ -478,10 +478,6 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         load_tw(tw, twg, GE::tw_n);
     }
     for (int i = threadIdx.x; i < 32 * 12; i += blockDim.x) (&wacc[0][0])[i] = 0.0;
-    // slots of the force partials this launch does not reach stay zero
-    if (!PM && blockIdx.x == 0)
-        for (int i = (int)gridDim.x * 6 + threadIdx.x; i < kp.nparts * 6; i += blockDim.x)
-            partial[(size_t)kp.part_off * 6 + i] = 0.0;
     __syncthreads();
     auto issue = [&](int b, int buf) {  // one thread
         fence_proxy_async();
@@ -842,7 +838,10 @@ k_xfwd(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ U, cplx<T>* _
 // fields, A (kept ky rows) -> B (all y rows); one staging buffer, refilled
 // once the first FFT stage has read it.
 // tm: A as {2 Kzp reals, n rows (x), 6 K planes (f K + ky)}.
-template <typename T, int N, int NF = 6>
+// KZP_: kz columns of the spectral arrays (compile time: the address
+// arithmetic folds into immediate offsets; the n x n x n/2 engines pass the
+// value of their z length).
+template <typename T, int N, int NF = 6, int KZP_ = Geo<T, N>::KZP>
 __global__ void __launch_bounds__(Geo<T, N>::CY2 * Geo<T, N>::G)
 k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -850,7 +849,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     using GE = Geo<T, N>;
     constexpr int CT = GE::CY2, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
-    const int KZP = kp.Kzp, NTZ = KZP / CT;
+    constexpr int KZP = KZP_, NTZ = KZP / CT;
     const int NITEM = kp.xsn * NTZ * NF;  // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -928,7 +927,7 @@ k_yinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 
 // pass 4: y-forward of the three fields, B (all y rows) -> A (kept ky rows).
 // tm: B as a 2-D array of 6 n n rows of 2 Kzp reals.
-template <typename T, int N, int CTV, int NF = 3>
+template <typename T, int N, int CTV, int NF = 3, int KZP_ = Geo<T, N>::KZP>
 __global__ void __launch_bounds__(CTV * Geo<T, N>::G)
 k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -937,7 +936,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     constexpr int CT = CTV, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "y-forward staging must be contiguous in y");
-    const int KZP = kp.Kzp, NTZ = KZP / CT;
+    constexpr int KZP = KZP_, NTZ = KZP / CT;
     const int NITEM = kp.xsn * NTZ * NF;   // items of this launch's x planes
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1027,7 +1026,7 @@ k_yfwd_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 // NF = 3: the plain x-inverse of three fields (one transform each, no curl).
 // tm: U (or the array being transformed) as 2-D rows of 2 Kzp reals, row
 // (f K + cy) K + cx.
-template <typename T, int N, int NF = 6>
+template <typename T, int N, int NF = 6, int KZP_ = Geo<T, N>::KZP>
 __global__ void __launch_bounds__(Geo<T, N>::CX1 * Geo<T, N>::G)
 k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twg,
            int* __restrict__ err) {
@@ -1036,8 +1035,8 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     using FFT = LineFFT<T, N, 1>;
     constexpr int CT = GE::CX1, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
-    const int KZP = kp.Kzp, NTZ = KZP / CT;
-    const int NTILE = K * NTZ;
+    constexpr int KZP = KZP_, NTZ = KZP / CT;
+    const int NTILE = kp.kyn * NTZ;   // tiles of this launch's ky rows
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -1063,7 +1062,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     auto issue = [&](int L) {  // one thread
         const int t = blockIdx.x + (L / 3) * gridDim.x, f = L % 3, buf = L & 1;
         if (t >= NTILE) return;
-        const int cy = t / NTZ, czt = t % NTZ;
+        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -1075,7 +1074,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     int ti = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
-        const int cy = t / NTZ, czt = t % NTZ;
+        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
         const int cz = czt * CT + col;
         const bool okz = cz < Kz;
         const T ky = ks * (T)cmode_of(cy, mmax, K);
@@ -1149,7 +1148,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
 // the gradient part the projection removes. Each field is transformed in
 // place in its staging buffer; kept outputs go to three result tiles.
 // tm: A as rows of 2 Kzp reals, row (f K + ky) n + x.
-template <typename T, int N, int MODE, bool SP = false>
+template <typename T, int N, int MODE, bool SP = false, int KZP_ = Geo<T, N>::KZP>
 __global__ void __launch_bounds__(Geo<T, N>::CX5 * Geo<T, N>::G)
 k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmu,
            const __grid_constant__ CUtensorMap tmh, KP kp, cplx<T>* __restrict__ U, cplx<T>* __restrict__ H,
@@ -1160,8 +1159,8 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
     constexpr int CT = GE::CX5, G = GE::G, K = GE::K;
     constexpr int NBOX = GE::nbox(N), BR = GE::brows(N), BP = GE::bpitch(N, CT), RS = NBOX * BP;
     static_assert(NBOX == 1 || BR == BP, "x-forward staging must be contiguous in x");
-    const int KZP = kp.Kzp, NTZ = KZP / CT;
-    const int NTILE = K * NTZ;
+    constexpr int KZP = KZP_, NTZ = KZP / CT;
+    const int NTILE = kp.kyn * NTZ;   // tiles of this launch's ky rows
     constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][RS][CT]
@@ -1190,7 +1189,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
     auto issue = [&](int L) {  // one thread
         const int t = blockIdx.x + (L / NF) * gridDim.x, f = field(L % NF), buf = L & 1;
         if (t >= NTILE) return;
-        const int cy = t / NTZ, czt = t % NTZ;
+        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar[buf], NBOX * box_bytes);
         for (int b = 0; b < NBOX; ++b)
@@ -1204,7 +1203,7 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
     bool stop = false;
     constexpr int NBK = GE::nbox(K), BRK = GE::brows(K);
     for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
-        const int cy = t / NTZ, czt = t % NTZ;
+        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
         // U (first step) or Q of this tile is read only after the three
         // transforms: start pulling it into L2 now (measured: loading it into
         // registers here instead, held across the transforms, was slower)

@@ -36,6 +36,7 @@ namespace ps {
 
 struct MaskArgs {
     int n, nz;   // grid n x n x nz, spacing dx on every axis
+    int x_lo, x_hi;   // x-planes [x_lo, x_hi) rasterised (a slab of the sharded step; 0, n otherwise)
     double dx, tw, h;
     int profile;
     const double* xw;
@@ -208,8 +209,8 @@ __global__ void k_mask_tris(MaskWs m, MaskArgs a, double reach) {
     if (ok) {
         for (int r = 0; r < 3; ++r) {
             double l = ceil((lo[r] - reach) / a.dx), h = floor((hi[r] + reach) / a.dx);
-            l = fmax(l, 0.0);
-            h = fmin(h, (double)((r == 2 ? a.nz : a.n) - 1));
+            l = fmax(l, r == 0 ? (double)a.x_lo : 0.0);
+            h = fmin(h, r == 0 ? (double)(a.x_hi - 1) : (double)((r == 2 ? a.nz : a.n) - 1));
             i0[r] = (int)l;
             e[r] = h >= l ? (int)(h - l) + 1 : 0;
             const double ar = m.xg[3 * id[0] + r];
@@ -398,6 +399,7 @@ __global__ void k_mask_dense(MaskWs m, MaskArgs a, T* chi, T* us, uint8_t* flag)
     const size_t n = a.n, nz = a.nz, n3 = n * n * nz;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(p % nz), j = (int)((p / nz) % n), i = (int)(p / (n * nz));
+        if (i < a.x_lo || i >= a.x_hi) continue;
         T best = (T)3.0e38;
         int bt = 0;
         for (int t = 0; t < a.n_tri; ++t) {

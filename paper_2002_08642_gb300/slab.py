@@ -99,3 +99,101 @@ class SlabPlan:
         """All-reduce of the 6 force/moment partial sums (a float64 tensor)."""
         dist.all_reduce(FM, group=self.group)
         return FM
+
+
+class SlabContexts:
+    """P slabs of the sharded step as P contexts on one GPU (each with its
+    own workspace): every pass of the step runs as the slabs' share of it
+    (ps_slab_phase), the two exchanges are device-to-device block copies
+    between the slabs' x-pass arrays A in the layout of ``SlabPlan``, and the
+    force is the host sum of the slabs' partial forces. It exercises the
+    per-slab GPU passes and the exchange pattern of the multi-GPU step
+    without a second GPU.
+
+    ``solvers``: P ``Solver`` objects of the same grid and parameters, in
+    slab order; ``x_off``, ``ky_off``: P + 1 start offsets of the x-plane and
+    kept-ky-row partitions (``balanced``)."""
+
+    def __init__(self, solvers, x_off, ky_off):
+        from . import binding as B
+
+        self.B = B
+        self.s = list(solvers)
+        self.P = len(self.s)
+        self.xo, self.ko = list(x_off), list(ky_off)
+        self.A = []
+        for r, g in enumerate(self.s):
+            B.ps_slab_set(g.ctx, self.xo[r], self.xo[r + 1], self.ko[r], self.ko[r + 1])
+            K, _, Kzp = B.ps_grid_info(g.ctx)
+            ptr, nbytes = B.ps_slab_buffer(g.ctx)
+            off = ptr - g.workspace.data_ptr()
+            cdt = torch.complex128 if g.dtype == torch.float64 else torch.complex64
+            self.A.append(g.workspace[off:off + nbytes].view(cdt).view(6, K, g.n, Kzp))
+        self.K = K
+
+    def _phase(self, ph):
+        for g in self.s:
+            self.B.ps_slab_phase(g.ctx, ph)
+
+    def ky_to_x(self):
+        """After the x-inverse: slab r gets rows ky in slab s's range at its
+        own x-planes from slab s (six fields)."""
+        for r in range(self.P):
+            x0, x1 = self.xo[r], self.xo[r + 1]
+            for s in range(self.P):
+                if s != r:
+                    k0, k1 = self.ko[s], self.ko[s + 1]
+                    self.A[r][:, k0:k1, x0:x1].copy_(self.A[s][:, k0:k1, x0:x1])
+
+    def x_to_ky(self):
+        """After the y-forward: slab r gets its ky rows at slab s's x-planes
+        from slab s (three fields)."""
+        for r in range(self.P):
+            k0, k1 = self.ko[r], self.ko[r + 1]
+            for s in range(self.P):
+                if s != r:
+                    x0, x1 = self.xo[s], self.xo[s + 1]
+                    self.A[r][:3, k0:k1, x0:x1].copy_(self.A[s][:3, k0:k1, x0:x1])
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            self._phase(0)
+            self.ky_to_x()
+            self._phase(1)
+            self.x_to_ky()
+            self._phase(2)
+
+    def forces(self):
+        """F and M of the last step: the sum of the slabs' shares (host, double)."""
+        F = [0.0, 0.0, 0.0]
+        M = [0.0, 0.0, 0.0]
+        for g in self.s:
+            f, m = g.forces()
+            F = [a + b for a, b in zip(F, f)]
+            M = [a + b for a, b in zip(M, m)]
+        return F, M
+
+    def state(self):
+        """The global spectral state (U, H) assembled from the slabs' ky rows,
+        as a state buffer of the first slab's size (ps_save_state layout)."""
+        K, n = self.K, self.s[0].n
+        bufs = []
+        for g in self.s:
+            b = g.state_buffer()
+            g.save_state(b)
+            bufs.append(b)
+        out = bufs[0].clone()
+        cdt = torch.complex128 if self.s[0].dtype == torch.float64 else torch.complex64
+        es = torch.finfo(self.s[0].dtype).bits // 4   # bytes per complex
+        nb = (out.numel() - 256) // 2                   # bytes of U (and of H)
+        Kzp = nb // (3 * K * K * es)
+
+        def view(b, which):
+            o = 256 + which * nb
+            return b[o:o + nb].view(cdt).view(3, K, K, Kzp)
+
+        for r in range(1, self.P):
+            k0, k1 = self.ko[r], self.ko[r + 1]
+            for which in (0, 1):
+                view(out, which)[:, k0:k1].copy_(view(bufs[r], which)[:, k0:k1])
+        return out
