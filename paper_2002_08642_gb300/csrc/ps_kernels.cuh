@@ -57,6 +57,11 @@
 #ifndef PS_Z3
 #define PS_Z3 1
 #endif
+// 1: the x-inverse reads Ux, Uy back from its output for the vorticity
+// instead of holding them in registers across its transforms
+#ifndef PS_X1_REREAD
+#define PS_X1_REREAD 1
+#endif
 // 1: z-pass line transforms whose threads fit in one warp sync by warp
 #ifndef PS_ZWS
 #define PS_ZWS 1
@@ -1070,7 +1075,9 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     };
     if (threadIdx.x == 0) issue(0);
     auto addr = [&](int p) { return p * CT + col; };
+#if !PS_X1_REREAD
     C2 R1[FFT::SLOTS], R2[FFT::SLOTS];
+#endif
     int ti = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
@@ -1112,6 +1119,29 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                         if (okz) o[f * AS] = v;
                         return;
                     }
+#if PS_X1_REREAD
+                    // Ux and Uy are read back from A where the vorticity needs
+                    // them: this thread wrote those very elements in an earlier
+                    // transform (the slot -> x map is the same for all five),
+                    // so they come from L2 and hold no registers across the
+                    // transforms
+                    if (!okz) return;
+                    if (f == 0) {                       // Ux
+                        o[0] = v;
+                    } else if (f == 1 && d == 0) {      // Uy
+                        o[AS] = v;
+                    } else if (f == 1) {                // w_z = Dx Uy - i ky Ux
+                        const C2 u = o[0];
+                        o[5 * AS] = cmk<C2>(v.x + ky * u.y, v.y - ky * u.x);
+                    } else if (d == 0) {                // Uz; w_x = i (ky Uz - kz Uy)
+                        const C2 u = o[AS];
+                        o[2 * AS] = v;
+                        o[3 * AS] = cmk<C2>(-(ky * v.y - kz * u.y), ky * v.x - kz * u.x);
+                    } else {                            // w_y = i kz Ux - Dx Uz
+                        const C2 u = o[0];
+                        o[4 * AS] = cmk<C2>(-kz * u.y - v.x, kz * u.x - v.y);
+                    }
+#else
                     if (f == 0) {                       // Ux
                         R1[slot] = v;
                         if (okz) o[0] = v;
@@ -1131,6 +1161,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                         const C2 u = R1[slot];
                         if (okz) o[4 * AS] = cmk<C2>(-kz * u.y - v.x, kz * u.x - v.y);
                     }
+#endif
                 };
                 FFT::template run_bu<false>(W, tw, addr, g, load, store);
                 __syncthreads();
