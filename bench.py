@@ -206,12 +206,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def measured_traffic(kernel, n):
-    """DRAM bytes per launch of `kernel` at grid n, scaled from the ncu figure
-    in profiles/traffic.txt by the grid points; None if the kernel sources
-    changed since the counters were taken, or no figure exists."""
+TRAFFIC_SOURCES = ("ps_kernels.cuh", "ps_fft.cuh", "ps_async.cuh", "ps_engine.cuh")
+
+
+def sources_sha256():
     import hashlib
 
+    return hashlib.sha256(b"".join(open(os.path.join(ROOT, "paper_2002_08642_gb300", "csrc", f), "rb").read()
+                                   for f in TRAFFIC_SOURCES)).hexdigest()
+
+
+def measured_traffic(kernel, npts):
+    """DRAM bytes per launch of pass `kernel` on a grid of npts points,
+    scaled from the ncu figure in profiles/traffic.txt (a capture on a
+    smaller grid: every z line moves the same bytes per point) by the grid
+    points; None if the kernel sources changed since the counters were
+    taken, or no figure exists."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         kv = {}
@@ -221,11 +231,9 @@ def measured_traffic(kernel, n):
                 kv[k] = v.strip()
     except OSError:
         return None
-    src = b"".join(open(os.path.join(ROOT, "paper_2002_08642_gb300", "csrc", f), "rb").read()
-                   for f in ("ps_kernels.cuh", "ps_fft.cuh", "ps_async.cuh"))
-    if kv.get("kernel") != kernel or kv.get("sources_sha256") != hashlib.sha256(src).hexdigest():
+    if kv.get("sources_sha256") != sources_sha256() or kernel not in kv:
         return None
-    return float(kv["dram_bytes"]) * (n / float(kv["measured_n"])) ** 3
+    return float(kv[kernel]) * npts / float(kv["measured_points"])
 
 
 def wing_inputs(cfg, steps):
@@ -465,10 +473,17 @@ def run_ours(args, cfg):
                    "precision": cfg["precision"], "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": src, "traffic": measured_traffic(top, n),
+                     "frac": achieved / peak, "peak_source": src, "traffic": measured_traffic(top, npts),
                      "algorithmic_bytes_per_launch": ab[top]},
         "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
-                          "achieved_GBs": step_bytes / (ms / args.steps / 1e3) / 1e9},
+                          "achieved_GBs": step_bytes / (ms / args.steps / 1e3) / 1e9,
+                          "frac": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
+                          "passes": {k: {"ms": fft_passes[k][0] / max(fft_passes[k][1], 1),
+                                         "algorithmic_bytes": ab[k],
+                                         "GBs": ab[k] / (fft_passes[k][0] / max(fft_passes[k][1], 1) / 1e3) / 1e9,
+                                         "frac": ab[k] / (fft_passes[k][0] / max(fft_passes[k][1], 1) / 1e3)
+                                                 / 1e9 / peak,
+                                         "traffic": measured_traffic(k, npts)} for k in fft_passes}},
         "z_pass_alu": z_pass_alu,
         "passes_ms": {k: v[0] / max(v[1], 1) for k, v in passes.items()},
         "e2e": {"value": e2e, "unit": "Mpts*steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

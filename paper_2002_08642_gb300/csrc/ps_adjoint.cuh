@@ -102,8 +102,11 @@ __global__ void k_adj_spec2(KP kp, cplx<T>* __restrict__ lam, const cplx<T>* __r
 // Physical pointwise adjoint. u, w: velocity and vorticity of the step (3 x
 // n^3 each), overwritten by ubar and wbar; nb: inverse(G) (scaled here by
 // 1/n^3). Writes dJ/dchi and dJ/dus of this step.
+// Memory bound: the thirteen loads of a point are issued before its
+// arithmetic, with a register budget (four blocks of 256 threads per SM) that
+// keeps them all in flight.
 template <typename T>
-__global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w, const T* __restrict__ nb,
+__global__ void __launch_bounds__(256, 4) k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w, const T* __restrict__ nb,
                             const T* __restrict__ chi, const T* __restrict__ us, T* __restrict__ gchi,
                             T* __restrict__ gus) {
     const int n = kp.n, nz = kp.nz;
@@ -120,11 +123,13 @@ __global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w
         {
             const uint32_t q = p / unz, k = p - q * unz;
             const uint32_t i = q / un, j = q - i * un;
-            const T rx = (T)i * dx - x0, ry = (T)j * dx - y0;
-            const T nbx = nb[p] * invn3, nby = nb[n3 + p] * invn3, nbz = nb[2 * n3 + p] * invn3;
+            const T nbx0 = nb[p], nby0 = nb[n3 + p], nbz0 = nb[2 * n3 + p];
             const T ux = u[p], uy = u[n3 + p], uz = u[2 * n3 + p];
             const T wx = w[p], wy = w[n3 + p], wz = w[2 * n3 + p];
             const T c = chi[p];
+            const T sx = us[p], sy = us[n3 + p], sz = us[2 * n3 + p];
+            const T rx = (T)i * dx - x0, ry = (T)j * dx - y0;
+            const T nbx = nbx0 * invn3, nby = nby0 * invn3, nbz = nbz0 * invn3;
             const T ce = c * inv_eta;
             // ubar = w x nbar - c nbar ; wbar = nbar x u
             T bx = wy * nbz - wz * nby - ce * nbx;
@@ -135,7 +140,6 @@ __global__ void k_adj_point(KP kp, AdjW aw, T* __restrict__ u, T* __restrict__ w
             const T vz = nbx * uy - nby * ux;
             // dJ/dchi is needed at every cell (also where chi = 0); the force
             // and moment term uses dJ/dp = a + b x r, p = chi (u - us)
-            const T sx = us[p], sy = us[n3 + p], sz = us[2 * n3 + p];
             const T dx_ = ux - sx, dy_ = uy - sy, dz_ = uz - sz;
             const T rz = (T)k * dx - z0;
             const T gx = a0 + b1 * rz - b2 * ry;

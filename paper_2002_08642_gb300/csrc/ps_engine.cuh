@@ -129,8 +129,8 @@ template <typename T, int N, int NZ = N> struct Engine {
         if ((e = attr(k_yinv<T, N, 6>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 3>, sm_strided))) return e;
         if ((e = attr(k_yfwd<T, N>, sm_strided))) return e;
-        if ((e = attr(k_zpass<T, NZ>, sm_zp))) return e;
-        if ((e = attr(k_zpass<T, NZ, true>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ, false, false, N>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ, true, false, N>, sm_zp))) return e;
         if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_zinv_phys<T, NZ, 1>, sm_z))) return e;
@@ -140,7 +140,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 2>, sm_x5))) return e;
         int occ = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, NZ>, thr_zp, sm_zp))) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass<T, NZ, false, false, N>, thr_zp, sm_zp))) return e;
         if (occ < 1) occ = 1;
         const int nb = N * N / GZ::LZ;
         zgrid() = nsm * occ < nb ? nsm * occ : nb;
@@ -161,7 +161,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         if ((e = attr(k_xfwd_tma<T, N, 2, false, KZ_>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 3, false, KZ_>, sm_x5t))) return e;
         if ((e = attr(k_xfwd_tma<T, N, 0, true, KZ_>, sm_x5s))) return e;
-        if ((e = attr(k_zpass<T, NZ, false, true>, sm_zp))) return e;
+        if ((e = attr(k_zpass<T, NZ, false, true, N>, sm_zp))) return e;
         if ((e = attr(k_yfwd_tma<T, N, GE::CY4, 6, KZ_>, sm_y4))) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, true, KZ_>, thr_x5, sm_x5s)))
             return e;
@@ -192,11 +192,11 @@ template <typename T, int N, int NZ = N> struct Engine {
         if (!resume) k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
         if (sp)
-            k_zpass<T, NZ, false, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
+            k_zpass<T, NZ, false, true, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us,
                                                                      b.flag, b.partial, twz(b.tw), b.err, nullptr,
                                                                      (const T*)b.chi_sp, (C2*)b.B);
         else
-            k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+            k_zpass<T, NZ, false, false, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                         b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);
         if (ev) { cudaEventRecord(ev[5], s); cudaEventRecord(ev[6], s); }
         if (sp) k_yfwd_tma<T, N, GE::CY4, 6, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
@@ -280,7 +280,7 @@ template <typename T, int N, int NZ = N> struct Engine {
             k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         }
         C2* nout = b.N3 ? (C2*)b.N3 : (C2*)b.B;
-        k_zpass<T, NZ, true><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+        k_zpass<T, NZ, true, false, N><<<zgrid(), thr_zp, sm_zp, s>>>(k1, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                           b.partial, twz(b.tw), b.err, (T*)p, nullptr, nout);
         k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(b.N3 ? *b.tmN : *b.tmB, k1, (C2*)b.A, tw,
                                                                   b.err);
@@ -313,7 +313,7 @@ template <typename T, int N, int NZ = N> struct Engine {
             k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
         } else if (phase == 1) {
             k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, kp, (C2*)b.B, tw, b.err);
-            k_zpass<T, NZ><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
+            k_zpass<T, NZ, false, false, N><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
                                                         b.partial, twz(b.tw), b.err, nullptr, nullptr, (C2*)b.B);
             k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, kp, (C2*)b.A, tw, b.err);
         } else {

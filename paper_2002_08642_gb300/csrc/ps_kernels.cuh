@@ -57,11 +57,6 @@
 #ifndef PS_Z3
 #define PS_Z3 1
 #endif
-// 1: the x-inverse reads Ux, Uy back from its output for the vorticity
-// instead of holding them in registers across its transforms
-#ifndef PS_X1_REREAD
-#define PS_X1_REREAD 1
-#endif
 // 1: z-pass line transforms whose threads fit in one warp sync by warp
 #ifndef PS_ZWS
 #define PS_ZWS 1
@@ -427,13 +422,14 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 // [x][y][z]), leaves the force partials of the last step untouched and
 // writes its three result fields to Bo (Bo = B allowed), so that B can keep
 // u and omega of the state for the step that follows.
-// Template N is the z-line length (nz); the number of lines per x-plane
-// and the x-plane count are kp.n (n x n x nz grid).
+// Template N is the z-line length (nz), NY the number of lines per x-plane
+// and of x-planes (n; n x n x nz grid; compile time, it keeps the z pass's
+// registers below the three-blocks-per-SM cap).
 // SP (sponge term on): also s = chi_sp omega, transformed forward like n
 // (s_x + i s_y per line by the third thread group, s_z of line pairs by the
 // odd lines' second group, the groups that are otherwise idle) into B
 // fields 3..5.
-template <typename T, int N, bool PM = false, bool SP = false>
+template <typename T, int N, bool PM = false, bool SP = false, int NY = N>
 __global__ void __launch_bounds__(3 * Geo<T, N>::LZ * Geo<T, N>::G, Geo<T, N>::ZMINB)
 k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __restrict__ us,
         const uint8_t* __restrict__ flag, double* __restrict__ partial, const cplx<T>* __restrict__ twg,
@@ -450,7 +446,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     constexpr int GL = Z3 ? GM : G;
     constexpr bool WS = PS_ZWS != 0 && GL <= 32 && 32 % GL == 0;
     constexpr int TWM = Z3 ? (tw_count(M) > 0 ? tw_count(M) : 1) : 0;
-    const int nyl = kp.n;   // lines per x-plane (the line length is N)
+    constexpr int nyl = NY;   // lines per x-plane (= kp.n; the line length is N)
     const int b0 = kp.xs0 * nyl / LZ, b1 = (kp.xs0 + kp.xsn) * nyl / LZ;   // this launch's batches
     constexpr uint32_t fbytes = (uint32_t)(LZ * KZP * sizeof(C2));
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1075,9 +1071,7 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
     };
     if (threadIdx.x == 0) issue(0);
     auto addr = [&](int p) { return p * CT + col; };
-#if !PS_X1_REREAD
     C2 R1[FFT::SLOTS], R2[FFT::SLOTS];
-#endif
     int ti = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
@@ -1119,29 +1113,6 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                         if (okz) o[f * AS] = v;
                         return;
                     }
-#if PS_X1_REREAD
-                    // Ux and Uy are read back from A where the vorticity needs
-                    // them: this thread wrote those very elements in an earlier
-                    // transform (the slot -> x map is the same for all five),
-                    // so they come from L2 and hold no registers across the
-                    // transforms
-                    if (!okz) return;
-                    if (f == 0) {                       // Ux
-                        o[0] = v;
-                    } else if (f == 1 && d == 0) {      // Uy
-                        o[AS] = v;
-                    } else if (f == 1) {                // w_z = Dx Uy - i ky Ux
-                        const C2 u = o[0];
-                        o[5 * AS] = cmk<C2>(v.x + ky * u.y, v.y - ky * u.x);
-                    } else if (d == 0) {                // Uz; w_x = i (ky Uz - kz Uy)
-                        const C2 u = o[AS];
-                        o[2 * AS] = v;
-                        o[3 * AS] = cmk<C2>(-(ky * v.y - kz * u.y), ky * v.x - kz * u.x);
-                    } else {                            // w_y = i kz Ux - Dx Uz
-                        const C2 u = o[0];
-                        o[4 * AS] = cmk<C2>(-kz * u.y - v.x, kz * u.x - v.y);
-                    }
-#else
                     if (f == 0) {                       // Ux
                         R1[slot] = v;
                         if (okz) o[0] = v;
@@ -1161,7 +1132,6 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                         const C2 u = R1[slot];
                         if (okz) o[4 * AS] = cmk<C2>(-kz * u.y - v.x, kz * u.x - v.y);
                     }
-#endif
                 };
                 FFT::template run_bu<false>(W, tw, addr, g, load, store);
                 __syncthreads();
