@@ -193,6 +193,18 @@ __host__ __device__ constexpr bool size_ok(int n) {
 }
 
 // ----------------------------------------------------------- line transform
+// Tile address of a line stored with one padding element after every 16
+// (no bank conflicts for 16-element strides): base + p + p/16. Since
+// (a + 16 m) + (a + 16 m)/16 = pad(a) + 17 m for every a, a stage whose
+// input stride or output stride is a multiple of 16 addresses its elements
+// as a per-butterfly base plus compile-time offsets.
+struct Pad16 {
+    int base;
+    __device__ __forceinline__ int operator()(int p) const { return base + p + (p >> 4); }
+};
+template <class A> struct is_pad16 { static constexpr bool value = false; };
+template <> struct is_pad16<Pad16> { static constexpr bool value = true; };
+
 // Mask of this warp's lanes that exist (the block's last warp may be partial).
 __device__ __forceinline__ unsigned warp_lanes() {
     const int left = (int)blockDim.x - (int)(threadIdx.x & ~31u);
@@ -230,7 +242,10 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     struct NoHook {
         __device__ __forceinline__ void operator()() const {}
     };
-    template <int s, bool FROM_TILE, bool BU = false, class Addr, class Load, class Store, class Hook = NoHook>
+    // TS: the last stage writes its outputs back into the tile, in place
+    // (store is not called).
+    template <int s, bool FROM_TILE, bool BU = false, bool TS = false, class Addr, class Load, class Store,
+              class Hook = NoHook>
     static __device__ __forceinline__ void stage(C* tile, const C* tw, const Addr& addr, int g,
                                                  const Load& load, const Store& store, bool on, unsigned lanes,
                                                  const Hook& hook = Hook()) {
@@ -241,14 +256,19 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
         constexpr bool last = (s == S - 1);
         constexpr bool from_tile = (s > 0) || FROM_TILE;
         constexpr int two = tw_offset(N, s);
+        constexpr bool pad = is_pad16<Addr>::value;
         // one butterfly: inputs, twiddles, DFT
         auto gather = [&](int j, C* v) {
             const int k = j % Ls;
 #pragma unroll
             for (int t = 0; t < r; ++t) {
                 C x;
-                if constexpr (from_tile) x = tile[addr(j + t * NBF)];
-                else x = load(j + t * NBF);
+                if constexpr (from_tile) {
+                    if constexpr (pad && NBF % 16 == 0) x = tile[addr(j) + t * (NBF + NBF / 16)];
+                    else x = tile[addr(j + t * NBF)];
+                } else {
+                    x = load(j + t * NBF);
+                }
                 if constexpr (Ls > 1) {
                     if (t > 0) {
                         C w = tw[two + (t - 1) * Ls + k];
@@ -265,9 +285,13 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
 #pragma unroll
             for (int u = 0; u < r; ++u) {
                 const int o = (j - k) * r + k + u * Ls;
-                if constexpr (last) {
+                if constexpr (last && !TS) {
                     if constexpr (BU) store(b * r + u, o, v[u]);
                     else store(o, v[u]);
+                } else if constexpr (pad && Ls % 16 == 0) {
+                    tile[addr((j - k) * r + k) + u * (Ls + Ls / 16)] = v[u];
+                } else if constexpr (pad && Ls == 1 && r == 16) {
+                    tile[addr(16 * j) + u] = v[u];
                 } else {
                     tile[addr(o)] = v[u];
                 }
@@ -313,7 +337,7 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
         }
         if constexpr (!last) sync(lanes);
         if constexpr (s == 0 && !last) hook();
-        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU>(tile, tw, addr, g, load, store, on, lanes, hook);
+        if constexpr (s + 1 < S) stage<s + 1, FROM_TILE, BU, TS>(tile, tw, addr, g, load, store, on, lanes, hook);
     }
 
     template <bool FROM_TILE, class Addr, class Load, class Store>
@@ -334,6 +358,26 @@ template <typename T, int N, int SIGN, bool WS = false> struct LineFFT {
     static __device__ __forceinline__ void run_bu(C* tile, const C* tw, const Addr& addr, int g,
                                                   const Load& load, const Store& store) {
         stage<0, FROM_TILE, true>(tile, tw, addr, g, load, store, true, WS ? warp_lanes() : 0u);
+    }
+    // Outputs written back into the tile (natural order, in place).
+    template <bool FROM_TILE, class Addr, class Load>
+    static __device__ __forceinline__ void run_tile(C* tile, const C* tw, const Addr& addr, int g,
+                                                    const Load& load) {
+        auto nostore = [](int, C) {};
+        stage<0, FROM_TILE, false, true>(tile, tw, addr, g, load, nostore, true, WS ? warp_lanes() : 0u);
+    }
+    // Same, for the threads with on == true (see run_masked).
+    template <bool FROM_TILE, class Addr, class Load>
+    static __device__ __forceinline__ void run_tile_masked(C* tile, const C* tw, const Addr& addr, int g,
+                                                           const Load& load, bool on) {
+        auto nostore = [](int, C) {};
+        if constexpr (WS) {
+            const unsigned lanes = __ballot_sync(warp_lanes(), on);
+            if (!on) return;
+            stage<0, FROM_TILE, false, true>(tile, tw, addr, g, load, nostore, true, lanes);
+        } else {
+            stage<0, FROM_TILE, false, true>(tile, tw, addr, g, load, nostore, on, 0u);
+        }
     }
     // Same, for the threads with on == true. Block barriers: the others
     // still take part in them. Warp barriers (WS): the others leave at once

@@ -531,13 +531,16 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 v = cmk<C2>(v.x - (T)0.5 * w.x - sg * w.y, v.y - (T)0.5 * w.y + sg * w.x);
                 return cmul(v, tw3[(sub - 1) * M + q]);
             };
-            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-            LineFFT<T, M, 1, WS>::template run<false>(tiles, tw, addr, gm, load, store);
+            if constexpr (M % 16 == 0) {   // the sub-line starts on a padding group
+                LineFFT<T, M, 1, WS>::template run_tile<false>(tiles, tw, Pad16{tbase + zad(sub * M)}, gm, load);
+            } else {
+                auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
+                LineFFT<T, M, 1, WS>::template run<false>(tiles, tw, addr, gm, load, store);
+            }
         } else {
             const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
             const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
             const int tbase = (int)(tile(pl, pr) - tiles);
-            auto addr = [&](int p) { return tbase + zad(p); };
             auto load = [&](int q) -> C2 {
                 if (q < Kz) {
                     C2 a = fa[q], c = fb[q];
@@ -550,8 +553,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
                 }
                 return cmk<C2>((T)0, (T)0);
             };
-            auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-            LineFFT<T, N, 1, WS>::template run<false>(tiles, tw, addr, g, load, store);
+            LineFFT<T, N, 1, WS>::template run_tile<false>(tiles, tw, Pad16{tbase}, g, load);
         }
         __syncthreads();
         // one buffer: every read of it is done, the next batch may land
@@ -640,13 +642,16 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
             if constexpr (Z3) {
                 const int sub = g / GM, gm = g % GM;
-                auto addr = [&](int p) { return tbase + zad(sub * M + p); };
-                auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
-                LineFFT<T, M, -1, WS>::template run_masked<true>(tiles, tw, addr, gm, noload, store, active);
+                if constexpr (M % 16 == 0) {
+                    LineFFT<T, M, -1, WS>::template run_tile_masked<true>(tiles, tw, Pad16{tbase + zad(sub * M)}, gm,
+                                                                          noload, active);
+                } else {
+                    auto addr = [&](int p) { return tbase + zad(sub * M + p); };
+                    auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
+                    LineFFT<T, M, -1, WS>::template run_masked<true>(tiles, tw, addr, gm, noload, store, active);
+                }
             } else {
-                auto addr = [&](int p) { return tbase + zad(p); };
-                auto store = [&](int p, C2 v) { if (active) tiles[addr(p)] = v; };
-                LineFFT<T, N, -1, WS>::template run_masked<true>(tiles, tw, addr, g, noload, store, active);
+                LineFFT<T, N, -1, WS>::template run_tile_masked<true>(tiles, tw, Pad16{tbase}, g, noload, active);
             }
         }
         __syncthreads();
@@ -1393,14 +1398,14 @@ k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<
     load_tw(tw, twg, GE::tw_n);
     __syncthreads();
     {
-        auto addr = [&](int p) { return zaddr(p, line, LP); };
+        const Pad16 addr{line * LP};
         auto load = [&](int z) -> C2 { return cmk<C2>(u[po + z], u[N3 + po + z]); };
         auto store = [&](int p, C2 v) { t0[addr(p)] = v; };
         FFT::template run<false>(t0, tw, addr, g, load, store);
     }
     {
         const bool even = (line & 1) == 0;
-        auto addr = [&](int p) { return zaddr(p, line >> 1, LP); };
+        const Pad16 addr{(line >> 1) * LP};
         auto load = [&](int z) -> C2 { return cmk<C2>(u[2 * N3 + po + z], u[2 * N3 + po + N + z]); };
         auto store = [&](int p, C2 v) { t1[addr(p)] = v; };
         FFT::template run_masked<false>(t1, tw, addr, g, load, store, even);
@@ -1446,7 +1451,7 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     const size_t N3 = (size_t)kp.n * kp.n * N;
     const size_t po = (size_t)lid * N;
     load_tw(tw, twg, GE::tw_n);
-    auto addr = [&](int p) { return zaddr(p, line, LP); };
+    const Pad16 addr{line * LP};
     __syncthreads();
     // (A + i B) of two real lines from their half spectra a, b
     auto two = [&](const C2* fa, const C2* fb, int q) -> C2 {
