@@ -42,7 +42,6 @@ struct ps_ctx {
     bool mask_dense_dirty;    // chi/u_s may be nonzero outside the touched list
     CUtensorMap tmA, tmB;     // TMA descriptors of the y passes' inputs
     CUtensorMap tmU, tmA5;    // TMA descriptors of the x passes' inputs
-    CUtensorMap tmUc;         // U in boxes of the spectral-curl x-inverse
     CUtensorMap tmG;          // adjoint G (x-inverse input), with_adjoint only
     CUtensorMap tmUp, tmHp;   // U and H in x-forward boxes (L2 prefetch)
     CUtensorMap tmN;          // keep_uw: the pressure's N fields (y-forward input)
@@ -575,7 +574,6 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         if (!encode_planes(&c->tmA, c->b.A, c->fp64, kp.Kzp, (size_t)n, (size_t)6 * Kk, ops->cy2, ops->br2) ||
             !encode_rows(&c->tmB, c->b.B, c->fp64, (size_t)6 * n * n, kp.Kzp, ops->cy4, ops->br4) ||
             !encode_rows(&c->tmU, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1, ops->br2) ||
-            !encode_rows(&c->tmUc, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx1c, ops->br2) ||
             !encode_rows(&c->tmA5, c->b.A, c->fp64, (size_t)6 * Kk * n, kp.Kzp, ops->cx5, ops->br4) ||
             !encode_rows(&c->tmUp, c->b.U, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2) ||
             !encode_rows(&c->tmHp, c->b.H, c->fp64, (size_t)3 * Kk * Kk, kp.Kzp, ops->cx5, ops->br2)) {
@@ -585,7 +583,6 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
         c->b.tmA = &c->tmA;
         c->b.tmB = &c->tmB;
         c->b.tmU = &c->tmU;
-        c->b.tmUc = &c->tmUc;
         c->b.tmA5 = &c->tmA5;
         c->b.tmUp = &c->tmUp;
         c->b.tmHp = &c->tmHp;

@@ -22,7 +22,6 @@ struct Bufs {
     const CUtensorMap* tmA;  // A as {2 Kzp reals, n rows, 6 K planes} (y-inverse input)
     const CUtensorMap* tmB;  // B as rows of 2 Kzp reals (y-forward input)
     const CUtensorMap* tmU;  // U as rows of 2 Kzp reals (x-inverse input)
-    const CUtensorMap* tmUc; // U, box of the spectral-curl x-inverse
     const CUtensorMap* tmA5; // A as rows of 2 Kzp reals (x-forward input)
     const CUtensorMap* tmUp; // U, H as rows of 2 Kzp reals, x-forward box (L2 prefetch)
     const CUtensorMap* tmHp;
@@ -39,7 +38,6 @@ struct Ops {
     int n, nz, C, C5, LY, G;
     int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
     int cx1, cx5;             // TMA box widths of the x passes (heights br2, br4)
-    int cx1c;                 // box width of the spectral-curl x-inverse
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
     cudaError_t (*prepare)(int nsm, int* zblocks);
     // ev (nullable): kEvPerStep events (see kEvPerStep)
@@ -118,20 +116,6 @@ template <typename T, int N, int NZ = N> struct Engine {
         return g;
     }
     static constexpr int thr_x1 = GE::CX1 * GE::G;
-    static constexpr size_t sm_x1c = (size_t)GE::x1c_smem(GE::CX1C);
-    static constexpr int thr_x1c = GE::CX1C * GE::G;
-    static int& x1cgrid() {
-        static int g = 0;
-        return g;
-    }
-    // the step's x-inverse with the curl (u and omega into A fields 0..5)
-    static void xinv_curl(const KP& kp, const Bufs& b, cudaStream_t s) {
-        if constexpr (PS_X1_CURL6 != 0)
-            k_xinv_curl_tma<T, N, KZ_><<<x1cgrid(), thr_x1c, sm_x1c, s>>>(*b.tmUc, kp, (C2*)b.A, (const C2*)b.tw,
-                                                                      b.err);
-        else
-            k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, (const C2*)b.tw, b.err);
-    }
     static constexpr int thr_x5 = GE::CX5 * GE::G;
     static constexpr size_t sm_y2 = (size_t)GE::y2_smem(GE::CY2, GE::Y2NB);
     static constexpr size_t sm_y4 = (size_t)GE::y4_smem(GE::CY4);
@@ -184,10 +168,6 @@ template <typename T, int N, int NZ = N> struct Engine {
         x5sgrid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_tma<T, N, 6, KZ_>, thr_x1, sm_x1))) return e;
         x1grid() = nsm * (occ < 1 ? 1 : occ);
-        if ((e = attr(k_xinv_curl_tma<T, N, KZ_>, sm_x1c))) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_curl_tma<T, N, KZ_>, thr_x1c, sm_x1c)))
-            return e;
-        x1cgrid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, false, KZ_>, thr_x5, sm_x5t))) return e;
         x5grid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
@@ -207,7 +187,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         const bool sp = b.chi_sp != nullptr;   // sponge term: six-field z/y-forward variants
         if (ev) cudaEventRecord(ev[0], s);
-        if (!resume) xinv_curl(kp, b, s);
+        if (!resume) k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
         if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
         if (!resume) k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         if (ev) { cudaEventRecord(ev[3], s); cudaEventRecord(ev[4], s); }
@@ -296,7 +276,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         if (!resume) {
-            xinv_curl(k1, b, s);
+            k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
             k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         }
         C2* nout = b.N3 ? (C2*)b.N3 : (C2*)b.B;
@@ -319,7 +299,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        xinv_curl(k1, b, s);
+        k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         const size_t BS = (size_t)N * N * k1.Kzp;
         k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, twz(b.tw));
@@ -330,7 +310,7 @@ template <typename T, int N, int NZ = N> struct Engine {
     static cudaError_t slab_phase(const KP& kp, const Bufs& b, int phase, int first, cudaStream_t s) {
         const C2* tw = (const C2*)b.tw;
         if (phase == 0) {
-            xinv_curl(kp, b, s);
+            k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, kp, (C2*)b.A, tw, b.err);
         } else if (phase == 1) {
             k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, kp, (C2*)b.B, tw, b.err);
             k_zpass<T, NZ, false, false, N><<<zgrid(), thr_zp, sm_zp, s>>>(kp, (C2*)b.B, (const T*)b.chi, (const T*)b.us, b.flag,
@@ -348,7 +328,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         Ops o;
         o.n = N; o.nz = NZ; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
         o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
-        o.cx1 = GE::CX1; o.cx5 = GE::CX5; o.cx1c = GE::CX1C;
+        o.cx1 = GE::CX1; o.cx5 = GE::CX5;
         o.zblocks = 0;
         o.prepare = &prepare;
         o.step = &step;

@@ -84,16 +84,6 @@
 #ifndef PS_X1_SMEM_KB
 #define PS_X1_SMEM_KB 64
 #endif
-// x-inverse with the spectral curl: shared-memory budget in KiB (three
-// staging tiles and the work tile; 75 lets three blocks reside per SM)
-#ifndef PS_X1C_SMEM_KB
-#define PS_X1C_SMEM_KB 75
-#endif
-// 1: the step's x-inverse transforms the spectral curl (six transforms);
-// 0: five transforms with the vorticity assembled from two register sets
-#ifndef PS_X1_CURL6
-#define PS_X1_CURL6 1
-#endif
 #ifndef PS_X5_SMEM_KB
 #define PS_X5_SMEM_KB 200
 #endif
@@ -213,14 +203,6 @@ template <typename T, int N> struct Geo {
     static constexpr int y2_smem(int c, int nb = 2) {   // y inverse: nb staging (K rows) + work tile (N rows)
         return (int)sizeof(C2) * c * (nb * nbox(K) * bpitch(K, c) + N) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
-    static constexpr int x1c_smem(int c) {  // x-inverse, spectral curl: 3 staging (K rows) + work tile
-        return (int)sizeof(C2) * c * (3 * nbox(K) * bpitch(K, c) + N) + 256;
-    }
-    static constexpr int pick_x1c() {
-        int c = CW;
-        while (c > 2 && x1c_smem(c) > PS_X1C_SMEM_KB * 1024) c /= 2;
-        return c;
-    }
     static constexpr int y4_smem(int c) {   // y forward: 2 staging tiles of N rows, transformed in place
         return (int)sizeof(C2) * c * (2 * nbox(N) * bpitch(N, c)) + (int)sizeof(C2) * (tw_count(N) + 1) + 256;
     }
@@ -242,7 +224,6 @@ template <typename T, int N> struct Geo {
     static constexpr int CY2 = pick_c(2, PS_Y2_SMEM_KB, 16);
     static constexpr int CY4 = pick_c(4, PS_Y4_SMEM_KB, 16);
     static constexpr int CX1 = pick_c(1, PS_X1_SMEM_KB, 16);   // same smem shape as the y inverse, two buffers
-    static constexpr int CX1C = pick_x1c();                   // x-inverse with the spectral curl
     static constexpr int CX5 = pick_c(5, PS_X5_SMEM_KB, 128 / 16);
     static constexpr int tw_n = tw_count(N) > 0 ? tw_count(N) : 1;
 };
@@ -1159,128 +1140,6 @@ k_xinv_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ 
                 };
                 FFT::template run_bu<false>(W, tw, addr, g, load, store);
                 __syncthreads();
-            }
-        }
-    }
-}
-
-// pass 1 (TMA-staged), spectral curl: the x-inverse of u and of
-// omega_hat = i k x u_hat as six transforms per (cy, kz tile). Along an x
-// line ky and kz are constant and kx = (2 pi/L) m follows the mode, so each
-// vorticity component is formed in the first stage's loads from two staged
-// velocity fields:
-//   w_x = i (ky u_z - kz u_y),  w_y = i (kz u_x - kx u_z),  w_z = i (kx u_y - ky u_x).
-// The three velocity fields of a tile sit in three staging buffers (one
-// mbarrier each); a buffer is refilled for the next tile as soon as its last
-// transform has read it (order: u_x, w_z, w_y | u_y, w_x | u_z). No output is
-// held across transforms, so few registers are live and three blocks
-// reside per SM; the twiddles are read from global memory (L1) to leave the
-// shared memory to the tiles.
-// tm: U as 2-D rows of 2 Kzp reals, row (f K + cy) K + cx.
-template <typename T, int N, int KZP_ = Geo<T, N>::KZP>
-__global__ void __launch_bounds__(Geo<T, N>::CX1C * Geo<T, N>::G)
-k_xinv_curl_tma(const __grid_constant__ CUtensorMap tm, KP kp, cplx<T>* __restrict__ A,
-                const cplx<T>* __restrict__ twg, int* __restrict__ err) {
-    using C2 = cplx<T>;
-    using GE = Geo<T, N>;
-    using FFT = LineFFT<T, N, 1>;
-    constexpr int CT = GE::CX1C, G = GE::G, K = GE::K;
-    constexpr int NBOX = GE::nbox(K), BR = GE::brows(K), BP = GE::bpitch(K, CT), RS = NBOX * BP;
-    constexpr int KZP = KZP_, NTZ = KZP / CT;
-    const int NTILE = kp.kyn * NTZ;   // tiles of this launch's ky rows
-    constexpr uint32_t box_bytes = (uint32_t)(BR * CT * sizeof(C2));
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C2* S = reinterpret_cast<C2*>(smem_base128(smraw));   // [3][RS][CT]: u_x, u_y, u_z
-    if (smem_u32(S) & 127u) {
-        if (threadIdx.x == 0) atomicExch(err, 2);
-        return;
-    }
-    C2* W = S + 3 * RS * CT;                              // [N][CT]
-    __shared__ __align__(8) uint64_t bar[3];
-    const int col = threadIdx.x % CT, g = threadIdx.x / CT;
-    const int mmax = kp.mmax, Kz = kp.Kz;
-    const T ks = (T)kp.ks, ksz = (T)kp.ksz;
-    const size_t AS = (size_t)N * K * KZP;
-    if (threadIdx.x == 0) {
-        for (int f = 0; f < 3; ++f) mbar_init(&bar[f], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    // field f of tile iteration ti into buffer f (one thread)
-    auto issue = [&](int f, int ti) {
-        const int t = blockIdx.x + ti * gridDim.x;
-        if (t >= NTILE) return;
-        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&bar[f], NBOX * box_bytes);
-        for (int b = 0; b < NBOX; ++b)
-            tma_load_2d(S + (size_t)(f * RS + b * BP) * CT, &tm, 2 * czt * CT, (f * K + cy) * K + b * BR, &bar[f]);
-    };
-    if (threadIdx.x == 0)
-        for (int f = 0; f < 3; ++f) issue(f, 0);
-    auto addr = [&](int p) { return p * CT + col; };
-    // staged value of mode m (|m| <= mmax) of field f
-    auto at = [&](int f, int c) { return S[(size_t)f * RS * CT + ((c / BR) * BP + c % BR) * CT + col]; };
-    int ti = 0;
-    bool stop = false;
-    for (int t = blockIdx.x; t < NTILE && !stop; t += gridDim.x, ++ti) {
-        const int cy = kp.ky0 + t / NTZ, czt = t % NTZ;
-        const int cz = czt * CT + col;
-        const bool okz = cz < Kz;
-        const T ky = ks * (T)cmode_of(cy, mmax, K);
-        const T kz = ksz * (T)cz;
-        C2* out = A + cz;   // + f AS + arow(x, cy) KZP
-        const uint32_t par = (uint32_t)(ti & 1);
-        // job j: 0 u_x, 1 w_z, 2 w_y, 3 u_y, 4 w_x, 5 u_z; waits on a buffer
-        // before its first use, refills a buffer after its last use
-#pragma unroll 1
-        for (int j = 0; j < 6; ++j) {
-            const int need = j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 2 : -1;
-            if (need >= 0) {
-                const bool ok = mbar_wait(&bar[need], par);
-                if (__syncthreads_or(!ok)) {
-                    // a copy never completed: record it, let the copies in flight land, stop
-                    if (threadIdx.x == 0) {
-                        atomicExch(err, 1);
-                        for (int f = need; f < 3; ++f) mbar_wait(&bar[f], par);
-                    }
-                    stop = true;
-                    break;
-                }
-            }
-            auto load = [&](int q) -> C2 {
-                const int m = mode_of(q, N);
-                if (m > mmax || m < -mmax) return cmk<C2>((T)0, (T)0);
-                const int c = cidx_of(m, K);
-                const T kx = ks * (T)m;
-                C2 a;
-                if (j == 0) return at(0, c);
-                if (j == 3) return at(1, c);
-                if (j == 5) return at(2, c);
-                if (j == 1) {            // kx u_y - ky u_x
-                    const C2 uy = at(1, c), ux = at(0, c);
-                    a = cmk<C2>(kx * uy.x - ky * ux.x, kx * uy.y - ky * ux.y);
-                } else if (j == 2) {     // kz u_x - kx u_z
-                    const C2 ux = at(0, c), uz = at(2, c);
-                    a = cmk<C2>(kz * ux.x - kx * uz.x, kz * ux.y - kx * uz.y);
-                } else {                 // ky u_z - kz u_y
-                    const C2 uz = at(2, c), uy = at(1, c);
-                    a = cmk<C2>(ky * uz.x - kz * uy.x, ky * uz.y - kz * uy.y);
-                }
-                return cmk<C2>(-a.y, a.x);   // times i
-            };
-            // output field of job j: u_x 0, w_z 5, w_y 4, u_y 1, w_x 3, u_z 2
-            const int of = j == 0 ? 0 : j == 1 ? 5 : j == 2 ? 4 : j == 3 ? 1 : j == 4 ? 3 : 2;
-            auto store = [&](int x, C2 v) {
-                if (okz) out[of * AS + GE::arow(x, cy) * KZP] = v;
-            };
-            FFT::template run<false>(W, twg, addr, g, load, store);
-            __syncthreads();
-            // buffers whose last transform this was: refill for the next tile
-            if (threadIdx.x == 0) {
-                if (j == 2) issue(0, ti + 1);
-                if (j == 4) issue(1, ti + 1);
-                if (j == 5) issue(2, ti + 1);
             }
         }
     }
