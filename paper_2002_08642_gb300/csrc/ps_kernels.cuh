@@ -275,6 +275,92 @@ __device__ __forceinline__ void split3_out(C2 F0, C2 F1, C2 F2, const C2* tw3, i
                  F0.y - (T)0.5 * (G1.y + G2.y) + h3 * (G1.x - G2.x));
 }
 
+// The z pass's n = 3M split by mirror pairs of modes (q, m = M - q): one
+// thread serves both, so each staged input and each twiddle is read once for
+// all three sub-lines. Since e^{2 pi i b m / n} = e^{2 pi i b / 3}
+// conj(e^{2 pi i b q / n}), the mirror needs no twiddle of its own.
+// Tiles hold sub-line b at padded positions zaddr(b M + p).
+//
+// Inverse pre-butterfly: the input line Z = A + i B (A, B the half spectra of
+// two real fields, kz < M kept) gives v = Z[q], w = Z[q + 2M] = Z[n - m],
+// v' = Z[m], w' = Z[n - q], and with t_b = e^{2 pi i b q / n}:
+//   Y_b[q] = t_b (v + e^{2 pi i 2b/3} w),  Y_b[m] = conj(t_b) (e^{2 pi i b/3} v' + w').
+// q = 0 serves mode 0 (Z[2M] = 0; the kz = 0 inputs' imaginary parts,
+// round-off of real fields, dropped) and the self-mirror mode M/2.
+template <typename T, int M>
+__device__ __forceinline__ void split3_pre(const cplx<T>* fa, const cplx<T>* fb, const cplx<T>* tw3, cplx<T>* t,
+                                           int q) {
+    using C2 = cplx<T>;
+    const T h = (T)0.86602540378443864676;   // sin(2 pi / 3)
+    auto put = [&](int b, int p, C2 v) { t[zaddr(b * M + p, 0, 0)] = v; };
+    // x + e^{2 pi i 2/3} y, x + e^{-2 pi i 2/3} y  (e^{+-2 pi i 2/3} = (-1/2, -+h))
+    auto rm = [&](C2 x, C2 y) { return cmk<C2>(x.x - (T)0.5 * y.x + h * y.y, x.y - (T)0.5 * y.y - h * y.x); };
+    auto rp = [&](C2 x, C2 y) { return cmk<C2>(x.x - (T)0.5 * y.x - h * y.y, x.y - (T)0.5 * y.y + h * y.x); };
+    constexpr int H = M / 2;
+    const int qa = q == 0 ? H : q;
+    const C2 a = fa[qa], c = fb[qa];
+    const C2 v = cmk<C2>(a.x - c.y, a.y + c.x);    // Z[qa]
+    const C2 w2 = cmk<C2>(a.x + c.y, c.x - a.y);   // Z[n - qa]
+    const C2 t1 = tw3[qa], t2 = tw3[M + qa];
+    if (q == 0) {
+        const C2 z0 = cmk<C2>(fa[0].x, fb[0].x);
+        put(0, 0, z0);
+        put(1, 0, z0);
+        put(2, 0, z0);
+        // mode M/2: Z[M/2 + 2M] = Z[n - M/2]
+        put(0, H, cadd(v, w2));
+        put(1, H, cmul(rm(v, w2), t1));
+        put(2, H, cmul(rp(v, w2), t2));
+        return;
+    }
+    const int m = M - q;
+    const C2 a2 = fa[m], c2 = fb[m];
+    const C2 w = cmk<C2>(a2.x + c2.y, c2.x - a2.y);   // Z[q + 2M] = Z[n - m]
+    const C2 v2 = cmk<C2>(a2.x - c2.y, a2.y + c2.x);  // Z[m]
+    put(0, q, cadd(v, w));
+    put(1, q, cmul(rm(v, w), t1));
+    put(2, q, cmul(rp(v, w), t2));
+    put(0, m, cadd(v2, w2));
+    put(1, m, cmul(rp(w2, v2), cconj(t1)));
+    put(2, m, cmul(rm(w2, v2), cconj(t2)));
+}
+
+// Forward recombination of the sub-line spectra F_b (b = 0, 1, 2) of a tile
+// for the pair (k, m = M - k): with s_b = e^{2 pi i b k / n},
+// G_b = conj(s_b) F_b[k], H_b = s_b F_b[m] and w = e^{2 pi i / 3},
+//   Z[k] = F_0[k] + G_1 + G_2,      Z[n - m] = F_0[k] + w G_1 + w^2 G_2,
+//   Z[n - k] = F_0[m] + H_1 + H_2,  Z[m] = F_0[m] + w^2 H_1 + w H_2.
+// k = 0 gives Z[0] (twice) and the self-mirror mode M/2: zm = Z[M/2],
+// znm = Z[n - M/2].
+template <typename T, int M>
+__device__ __forceinline__ void split3_pair_out(const cplx<T>* t, const cplx<T>* tw3, int k, cplx<T>& zk,
+                                                cplx<T>& znk, cplx<T>& zm, cplx<T>& znm) {
+    using C2 = cplx<T>;
+    const T h = (T)0.86602540378443864676;
+    auto at = [&](int b, int p) { return t[zaddr(b * M + p, 0, 0)]; };
+    // x + w y + w^2 z
+    auto rw = [&](C2 x, C2 y, C2 z) {
+        return cmk<C2>(x.x - (T)0.5 * (y.x + z.x) - h * (y.y - z.y), x.y - (T)0.5 * (y.y + z.y) + h * (y.x - z.x));
+    };
+    constexpr int H = M / 2;
+    const int ka = k == 0 ? H : k;
+    const C2 s1 = tw3[ka], s2 = tw3[M + ka];
+    const C2 f0 = at(0, ka), g1 = cmul(at(1, ka), cconj(s1)), g2 = cmul(at(2, ka), cconj(s2));
+    if (k == 0) {
+        zk = cadd(at(0, 0), cadd(at(1, 0), at(2, 0)));
+        znk = zk;
+        zm = cadd(f0, cadd(g1, g2));
+        znm = rw(f0, g1, g2);
+        return;
+    }
+    const int m = M - k;
+    const C2 e0 = at(0, m), h1 = cmul(at(1, m), s1), h2 = cmul(at(2, m), s2);
+    zk = cadd(f0, cadd(g1, g2));
+    znm = rw(f0, g1, g2);
+    znk = cadd(e0, cadd(h1, h2));
+    zm = rw(e0, h2, h1);
+}
+
 // Integrating-factor AB2 update of one mode (Sec. 4.1, time stepping):
 // U^{n+1} = E U^n + (dt/2)(3 E N^n - E^2 N^{n-1}). The history array holds
 // Q^n = E U^n - (dt/2) E^2 N^{n-1}, the part of U^{n+1} known before N^n, so
@@ -417,7 +503,11 @@ k_yinv(KP kp, const cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, const cplx
 //          Z[2M + k'] = sum_b e^{-2 pi i 2b/3} e^{-2 pi i b k'/n} F_b[k'],
 // F_b the forward length-M transform of z[3a + b]; sub-line b of a tile
 // holds z[3a + b] at position b M + a, so the pointwise phase reads and
-// writes in place and no reordering pass is needed.
+// writes in place and no reordering pass is needed. The pre-butterfly (Y_b
+// into the tiles, then the inverse transforms in place) and the
+// recombination (fused with the unpack to B) each go by mirror pairs of
+// modes (split3_pre, split3_pair_out): every staged input, tile value and
+// twiddle is read once.
 // PM (pressure evaluation): also writes (1/2)|u|^2 to half_u2 (n^3,
 // [x][y][z]), leaves the force partials of the last step untouched and
 // writes its three result fields to Bo (Bo = B allowed), so that B can keep
@@ -510,32 +600,25 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         }
         const C2* st = stage + (size_t)buf * 6 * LZ * KZP;
         if constexpr (Z3) {
-            const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
-            const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
+            // the split's pre-butterfly once per mirror pair of modes, into the tiles
+            for (int idx = threadIdx.x; idx < 3 * LZ * (M / 2); idx += blockDim.x) {
+                const int ft = idx / (M / 2), q = idx % (M / 2);   // tile (l, p), ft = 3 l + p
+                const int l = ft / 3, p = ft % 3;
+                split3_pre<T, M>(st + (size_t)((2 * p) * LZ + l) * KZP, st + (size_t)((2 * p + 1) * LZ + l) * KZP,
+                                 tw3, tiles + (size_t)ft * LP, q);
+            }
+            __syncthreads();
+            // one buffer: every read of it is done, the next batch may land
+            if (NB == 1 && threadIdx.x == 0 && more) issue(b + gridDim.x, 0);
             const int sub = g / GM, gm = g % GM;
-            const int tbase = (int)(tile(pl, pr) - tiles) ;
-            auto addr = [&](int p) { return tbase + zad(sub * M + p); };
-            const T h3 = (T)0.86602540378443864676;   // sin(2 pi / 3)
-            auto load = [&](int q) -> C2 {
-                C2 a = fa[q], c = fb[q];
-                if (q == 0) { a.y = 0; c.y = 0; }
-                C2 v = cmk<C2>(a.x - c.y, a.y + c.x);                      // Z[q]
-                C2 w = cmk<C2>((T)0, (T)0);
-                if (q > 0) {
-                    const C2 a2 = fa[M - q], c2 = fb[M - q];
-                    w = cmk<C2>(a2.x + c2.y, c2.x - a2.y);                 // Z[q + 2M]
-                }
-                if (sub == 0) return cadd(v, w);
-                // e^{2 pi i 2 sub / 3}: sub 1 -> (-1/2, -h), sub 2 -> (-1/2, +h)
-                const T sg = sub == 1 ? -h3 : h3;
-                v = cmk<C2>(v.x - (T)0.5 * w.x - sg * w.y, v.y - (T)0.5 * w.y + sg * w.x);
-                return cmul(v, tw3[(sub - 1) * M + q]);
-            };
+            const int tbase = (int)(tile(pl, pr) - tiles);
+            auto noload = [&](int) -> C2 { return cmk<C2>((T)0, (T)0); };
             if constexpr (M % 16 == 0) {   // the sub-line starts on a padding group
-                LineFFT<T, M, 1, WS>::template run_tile<false>(tiles, tw, Pad16{tbase + zad(sub * M)}, gm, load);
+                LineFFT<T, M, 1, WS>::template run_tile<true>(tiles, tw, Pad16{tbase + zad(sub * M)}, gm, noload);
             } else {
+                auto addr = [&](int p) { return tbase + zad(sub * M + p); };
                 auto store = [&](int p, C2 v) { tiles[addr(p)] = v; };
-                LineFFT<T, M, 1, WS>::template run<false>(tiles, tw, addr, gm, load, store);
+                LineFFT<T, M, 1, WS>::template run<true>(tiles, tw, addr, gm, noload, store);
             }
         } else {
             const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
@@ -557,7 +640,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
         }
         __syncthreads();
         // one buffer: every read of it is done, the next batch may land
-        if (NB == 1 && threadIdx.x == 0 && more) issue(b + gridDim.x, 0);
+        if (!Z3 && NB == 1 && threadIdx.x == 0 && more) issue(b + gridDim.x, 0);
         double fm[6] = {0, 0, 0, 0, 0, 0};
         bool touched = false;
         // n = u x w - (chi/eta)(u - us) of line l at z; forces in double
@@ -655,48 +738,66 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             }
         }
         __syncthreads();
-        if constexpr (Z3) {
-            // radix-3 recombination of the three sub-line spectra, kept modes only
-            const T h3 = (T)0.86602540378443864676;
-            constexpr int NREC = SP ? 3 * LZ : LZ + LZ / 2;   // transformed tiles
-            for (int idx = threadIdx.x; idx < NREC * M; idx += blockDim.x) {
-                const int fl2 = idx / M, kq = idx % M;
-                C2* t = SP ? tile(fl2 % LZ, fl2 / LZ) : (fl2 < LZ ? tile(fl2, 0) : tile(2 * (fl2 - LZ), 1));
-                const C2 F0 = t[zad(kq)], F1 = t[zad(M + kq)], F2 = t[zad(2 * M + kq)];
-                const C2 G1 = cmul(F1, cconj(tw3[kq])), G2 = cmul(F2, cconj(tw3[M + kq]));
-                const C2 Zk = cadd(F0, cadd(G1, G2));
-                // e^{-2 pi i 2/3} = (-1/2, +h), e^{-2 pi i 4/3} = (-1/2, -h)
-                const C2 Zm = cmk<C2>(F0.x - (T)0.5 * (G1.x + G2.x) - h3 * (G1.y - G2.y),
-                                      F0.y - (T)0.5 * (G1.y + G2.y) + h3 * (G1.x - G2.x));
-                t[zad(kq)] = Zk;
-                t[zad(2 * M + kq)] = Zm;
-            }
-            __syncthreads();
-        }
-        // unpack the two-for-one transforms, keep kz < Kz
         C2* const Bw = PM ? Bo : B;
-        for (int idx = threadIdx.x; idx < LZ * Kz; idx += blockDim.x) {
-            const int l = idx / Kz, k = idx % Kz;
-            const size_t lo = ((size_t)b * LZ + l) * KZP;
-            const C2* t0 = tile(l, 0);
-            const C2* t1 = tile(l & ~1, 1);
-            const int m = (N - k) % N;
-            const C2 zk = t0[zad(k)], zm = t0[zad(m)];
-            // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
-            Bw[lo + k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-            Bw[BS + lo + k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
-            const C2 wk = t1[zad(k)], wm = t1[zad(m)];
-            Bw[2 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
-                                          : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
-            if constexpr (SP) {
-                const C2* t2 = tile(l, 2);
-                const C2* t3 = tile(l | 1, 1);
-                const C2 sk = t2[zad(k)], sm = t2[zad(m)];
-                B[3 * BS + lo + k] = cmk<C2>((T)0.5 * (sk.x + sm.x), (T)0.5 * (sk.y - sm.y));
-                B[4 * BS + lo + k] = cmk<C2>((T)0.5 * (sk.y + sm.y), (T)0.5 * (sm.x - sk.x));
-                const C2 qk = t3[zad(k)], qm = t3[zad(m)];
-                B[5 * BS + lo + k] = (l & 1) ? cmk<C2>((T)0.5 * (qk.y + qm.y), (T)0.5 * (qm.x - qk.x))
-                                             : cmk<C2>((T)0.5 * (qk.x + qm.x), (T)0.5 * (qk.y - qm.y));
+        // P = (Z_k + conj Z_{-k}) / 2 and Q = (Z_k - conj Z_{-k}) / (2 i) of a two-for-one transform
+        auto P2 = [](C2 zk, C2 zm) { return cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)); };
+        auto Q2 = [](C2 zk, C2 zm) { return cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x)); };
+        if constexpr (Z3) {
+            // radix-3 recombination of the sub-line spectra by mirror pairs of
+            // kept modes, unpacked straight to B: tile (l, 0) -> fields 0, 1 of
+            // line l; (l, 1), l even -> field 2 of lines l, l + 1; with the
+            // sponge also (l, 2) -> fields 3, 4 of line l and (l, 1), l odd ->
+            // field 5 of lines l - 1, l
+            constexpr int NT = SP ? 3 * LZ : LZ + LZ / 2;   // transformed tiles
+            for (int idx = threadIdx.x; idx < NT * (M / 2); idx += blockDim.x) {
+                const int tj = idx / (M / 2), k = idx % (M / 2);
+                const int l = SP ? tj % LZ : (tj < LZ ? tj : 2 * (tj - LZ));
+                const int p = SP ? tj / LZ : (tj < LZ ? 0 : 1);
+                const size_t lo = ((size_t)b * LZ + l) * KZP;
+                C2 *dP, *dQ;
+                if (p == 0) {
+                    dP = Bw + lo;
+                    dQ = Bw + BS + lo;
+                } else if (p == 2) {
+                    dP = B + 3 * BS + lo;
+                    dQ = B + 4 * BS + lo;
+                } else if ((l & 1) == 0) {
+                    dP = Bw + 2 * BS + lo;
+                    dQ = Bw + 2 * BS + lo + KZP;
+                } else {
+                    dP = B + 5 * BS + lo - KZP;
+                    dQ = B + 5 * BS + lo;
+                }
+                C2 zk, znk, zm, znm;
+                split3_pair_out<T, M>(tile(l, p), tw3, k, zk, znk, zm, znm);
+                const int k2 = k == 0 ? M / 2 : M - k;
+                dP[k] = P2(zk, znk);
+                dQ[k] = Q2(zk, znk);
+                dP[k2] = P2(zm, znm);
+                dQ[k2] = Q2(zm, znm);
+            }
+        } else {
+            // unpack the two-for-one transforms, keep kz < Kz
+            for (int idx = threadIdx.x; idx < LZ * Kz; idx += blockDim.x) {
+                const int l = idx / Kz, k = idx % Kz;
+                const size_t lo = ((size_t)b * LZ + l) * KZP;
+                const C2* t0 = tile(l, 0);
+                const C2* t1 = tile(l & ~1, 1);
+                const int m = (N - k) % N;
+                const C2 zk = t0[zad(k)], zm = t0[zad(m)];
+                Bw[lo + k] = P2(zk, zm);
+                Bw[BS + lo + k] = Q2(zk, zm);
+                const C2 wk = t1[zad(k)], wm = t1[zad(m)];
+                Bw[2 * BS + lo + k] = (l & 1) ? Q2(wk, wm) : P2(wk, wm);
+                if constexpr (SP) {
+                    const C2* t2 = tile(l, 2);
+                    const C2* t3 = tile(l | 1, 1);
+                    const C2 sk = t2[zad(k)], sm = t2[zad(m)];
+                    B[3 * BS + lo + k] = P2(sk, sm);
+                    B[4 * BS + lo + k] = Q2(sk, sm);
+                    const C2 qk = t3[zad(k)], qm = t3[zad(m)];
+                    B[5 * BS + lo + k] = (l & 1) ? Q2(qk, qm) : P2(qk, qm);
+                }
             }
         }
         __syncthreads();
