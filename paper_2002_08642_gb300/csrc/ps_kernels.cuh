@@ -287,12 +287,20 @@ __device__ __forceinline__ void split3_out(C2 F0, C2 F1, C2 F2, const C2* tw3, i
 //   Y_b[q] = t_b (v + e^{2 pi i 2b/3} w),  Y_b[m] = conj(t_b) (e^{2 pi i b/3} v' + w').
 // q = 0 serves mode 0 (Z[2M] = 0; the kz = 0 inputs' imaginary parts,
 // round-off of real fields, dropped) and the self-mirror mode M/2.
+// Padded tile position of entry p of sub-line b (sub-lines of length M):
+// zaddr(b M + p) = b (M + M/16) + zaddr(p) when 16 divides M.
+template <int M>
+__device__ __forceinline__ int zsub(int b, int p) {
+    if constexpr (M % 16 == 0) return b * (M + M / 16) + p + (p >> 4);
+    else return zaddr(b * M + p, 0, 0);
+}
+
 template <typename T, int M>
 __device__ __forceinline__ void split3_pre(const cplx<T>* fa, const cplx<T>* fb, const cplx<T>* tw3, cplx<T>* t,
                                            int q) {
     using C2 = cplx<T>;
     const T h = (T)0.86602540378443864676;   // sin(2 pi / 3)
-    auto put = [&](int b, int p, C2 v) { t[zaddr(b * M + p, 0, 0)] = v; };
+    auto put = [&](int b, int p, C2 v) { t[zsub<M>(b, p)] = v; };
     // x + e^{2 pi i 2/3} y, x + e^{-2 pi i 2/3} y  (e^{+-2 pi i 2/3} = (-1/2, -+h))
     auto rm = [&](C2 x, C2 y) { return cmk<C2>(x.x - (T)0.5 * y.x + h * y.y, x.y - (T)0.5 * y.y - h * y.x); };
     auto rp = [&](C2 x, C2 y) { return cmk<C2>(x.x - (T)0.5 * y.x - h * y.y, x.y - (T)0.5 * y.y + h * y.x); };
@@ -337,7 +345,7 @@ __device__ __forceinline__ void split3_pair_out(const cplx<T>* t, const cplx<T>*
                                                 cplx<T>& znk, cplx<T>& zm, cplx<T>& znm) {
     using C2 = cplx<T>;
     const T h = (T)0.86602540378443864676;
-    auto at = [&](int b, int p) { return t[zaddr(b * M + p, 0, 0)]; };
+    auto at = [&](int b, int p) { return t[zsub<M>(b, p)]; };
     // x + w y + w^2 z
     auto rw = [&](C2 x, C2 y, C2 z) {
         return cmk<C2>(x.x - (T)0.5 * (y.x + z.x) - h * (y.y - z.y), x.y - (T)0.5 * (y.y + z.y) + h * (y.x - z.x));
@@ -550,6 +558,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
     C2* tw = tiles + 3 * LZ * LP;
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double wacc[32][12];     // per-warp (sum, compensation) of the six sums
+    __shared__ uint8_t sflag[LZ];       // mask flags of the batch's lines
     const int fl = threadIdx.x / G, g = threadIdx.x % G;
     const int pl = fl / 3, pr = fl % 3;
     const int Kz = kp.Kz;
@@ -599,13 +608,17 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             break;
         }
         const C2* st = stage + (size_t)buf * 6 * LZ * KZP;
+        // the batch's mask flags: loaded now, stored to shared memory after
+        // the inverse transforms, read by the pointwise phase
+        const uint8_t myflag = threadIdx.x < LZ ? flag[(size_t)b * LZ + threadIdx.x] : (uint8_t)0;
         if constexpr (Z3) {
-            // the split's pre-butterfly once per mirror pair of modes, into the tiles
-            for (int idx = threadIdx.x; idx < 3 * LZ * (M / 2); idx += blockDim.x) {
-                const int ft = idx / (M / 2), q = idx % (M / 2);   // tile (l, p), ft = 3 l + p
-                const int l = ft / 3, p = ft % 3;
-                split3_pre<T, M>(st + (size_t)((2 * p) * LZ + l) * KZP, st + (size_t)((2 * p + 1) * LZ + l) * KZP,
-                                 tw3, tiles + (size_t)ft * LP, q);
+            // the split's pre-butterfly once per mirror pair of modes, into the
+            // tiles; each thread group fills its own tile (pl, pr)
+            {
+                const C2* fa = st + (size_t)((2 * pr) * LZ + pl) * KZP;
+                const C2* fb = st + (size_t)((2 * pr + 1) * LZ + pl) * KZP;
+                C2* t = tile(pl, pr);
+                for (int q = g; q < M / 2; q += G) split3_pre<T, M>(fa, fb, tw3, t, q);
             }
             __syncthreads();
             // one buffer: every read of it is done, the next batch may land
@@ -638,6 +651,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             };
             LineFFT<T, N, 1, WS>::template run_tile<false>(tiles, tw, Pad16{tbase}, g, load);
         }
+        if (threadIdx.x < LZ) sflag[threadIdx.x] = myflag;
         __syncthreads();
         // one buffer: every read of it is done, the next batch may land
         if (!Z3 && NB == 1 && threadIdx.x == 0 && more) issue(b + gridDim.x, 0);
@@ -652,7 +666,7 @@ k_zpass(KP kp, cplx<T>* __restrict__ B, const T* __restrict__ chi, const T* __re
             ny = uz * wx - ux * wz;
             nz = ux * wy - uy * wx;
             if constexpr (PM) half_u2[(size_t)lid * N + z] = (T)0.5 * (ux * ux + uy * uy + uz * uz);
-            if (flag[lid] != 0) {
+            if (sflag[l] != 0) {
                 const size_t po = (size_t)lid * N + z;
                 const T c = chi[po];
                 if (c != (T)0) {
