@@ -79,6 +79,21 @@ template <typename T, int N, int NZ = N> struct Engine {
     static constexpr int thr_5 = GE::C5 * GE::G;
     static constexpr int thr_z = GZ::LY * GZ::G;
     static constexpr int thr_zp = 3 * GZ::LZ * GZ::G;
+    // persistent physical <-> z-spectral transforms
+    using ZP = ZPhys<T, NZ>;
+    static constexpr size_t sm_zi = (size_t)ZP::smem(ZP::LI, false);
+    static constexpr size_t sm_zf = (size_t)ZP::smem(ZP::LF, true);
+    static constexpr int thr_zi = ZP::threads(ZP::LI);
+    static constexpr int thr_zf = ZP::threads(ZP::LF);
+    static_assert((N * N) % ZP::LI == 0 && (N * N) % ZP::LF == 0, "z-line batches divide the lines");
+    static int& zigrid() {
+        static int g = 0;
+        return g;
+    }
+    static int& zfgrid() {
+        static int g = 0;
+        return g;
+    }
     // twiddles of the z lines: the table of length-NZ lines sits after the
     // length-N one when the lengths differ
     static const C2* twz(const void* tw) { return (const C2*)tw + (NZ == N ? 0 : 3 * N); }
@@ -133,9 +148,9 @@ template <typename T, int N, int NZ = N> struct Engine {
         if ((e = attr(k_zpass<T, NZ, true, false, N>, sm_zp))) return e;
         if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
-        if ((e = attr(k_zinv_phys<T, NZ, 1>, sm_z))) return e;
-        if ((e = attr(k_zfwd_phys<T, NZ>, sm_z))) return e;
-        if ((e = attr(k_zinv_phys<T, NZ>, sm_z))) return e;
+        if ((e = attr(k_zinv_sub<T, NZ>, sm_z))) return e;
+        if ((e = attr(k_zfwd_phys<T, NZ>, sm_zf))) return e;
+        if ((e = attr(k_zinv_phys<T, NZ>, sm_zi))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 1>, sm_x5))) return e;
         if ((e = attr(k_xfwd<T, N, 2>, sm_x5))) return e;
@@ -170,6 +185,10 @@ template <typename T, int N, int NZ = N> struct Engine {
         x1grid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_tma<T, N, 0, false, KZ_>, thr_x5, sm_x5t))) return e;
         x5grid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zinv_phys<T, NZ>, thr_zi, sm_zi))) return e;
+        zigrid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zfwd_phys<T, NZ>, thr_zf, sm_zf))) return e;
+        zfgrid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
     }
 
@@ -216,7 +235,7 @@ template <typename T, int N, int NZ = N> struct Engine {
 
     static cudaError_t set_velocity(const KP& kp, const Bufs& b, const void* u, cudaStream_t s) {
         const C2* tw = (const C2*)b.tw;
-        k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const T*)u, (C2*)b.B, twz(b.tw));
+        k_zfwd_phys<T, NZ><<<zfgrid(), thr_zf, sm_zf, s>>>(kp, (const T*)u, (C2*)b.B, twz(b.tw), b.err);
         k_yfwd<T, N><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.B, (C2*)b.A, tw);
         k_xfwd_tma<T, N, 1, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, kp, (C2*)b.U, (C2*)b.H,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
@@ -227,7 +246,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)b.U, (C2*)b.A, tw);
         k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)u, twz(b.tw));
+        k_zinv_phys<T, NZ><<<zigrid(), thr_zi, sm_zi, s>>>(kp, (const C2*)b.B, (T*)u, twz(b.tw), b.err);
         return cudaGetLastError();
     }
 
@@ -235,7 +254,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         k_xinv<T, N, 3><<<grid_xs(kp, GE::C), thr_s, sm_strided, s>>>(kp, (const C2*)spec, (C2*)b.A, tw);
         k_yinv<T, N, 3><<<grid_ys(kp), thr_s, sm_strided, s>>>(kp, (const C2*)b.A, (C2*)b.B, tw);
-        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(kp, (const C2*)b.B, (T*)phys, twz(b.tw));
+        k_zinv_phys<T, NZ><<<zigrid(), thr_zi, sm_zi, s>>>(kp, (const C2*)b.B, (T*)phys, twz(b.tw), b.err);
         return cudaGetLastError();
     }
 
@@ -243,7 +262,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         const C2* tw = (const C2*)b.tw;
         KP k1 = kp;
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
-        k_zfwd_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const T*)phys, (C2*)b.B, twz(b.tw));
+        k_zfwd_phys<T, NZ><<<zfgrid(), thr_zf, sm_zf, s>>>(k1, (const T*)phys, (C2*)b.B, twz(b.tw), b.err);
         k_yfwd_tma<T, N, GE::CY4, 3, KZ_><<<y4grid(), thr_y4, sm_y4, s>>>(*b.tmB, k1, (C2*)b.A, tw, b.err);
         k_xfwd_tma<T, N, 2, false, KZ_><<<x5grid(), thr_x5, sm_x5t, s>>>(*b.tmA5, *b.tmUp, *b.tmHp, k1, (C2*)spec, nullptr,
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
@@ -258,7 +277,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         k1.xs0 = 0; k1.xsn = N; k1.part_off = 0;
         k_xinv_tma<T, N, 3, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmG, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N, 3, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
-        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)phys, twz(b.tw));
+        k_zinv_phys<T, NZ><<<zigrid(), thr_zi, sm_zi, s>>>(k1, (const C2*)b.B, (T*)phys, twz(b.tw), b.err);
         return cudaGetLastError();
     }
 
@@ -289,7 +308,7 @@ template <typename T, int N, int NZ = N> struct Engine {
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
         k_yinv_tma<T, N, 1, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
-        k_zinv_phys<T, NZ, 1><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw));
+        k_zinv_sub<T, NZ><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw));
         return cudaGetLastError();
     }
 
@@ -302,8 +321,8 @@ template <typename T, int N, int NZ = N> struct Engine {
         k_xinv_tma<T, N, 6, KZ_><<<x1grid(), thr_x1, sm_x1, s>>>(*b.tmU, k1, (C2*)b.A, tw, b.err);
         k_yinv_tma<T, N, 6, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, (C2*)b.B, tw, b.err);
         const size_t BS = (size_t)N * N * k1.Kzp;
-        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B, (T*)u, twz(b.tw));
-        k_zinv_phys<T, NZ><<<zblocks(), thr_z, sm_z, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, twz(b.tw));
+        k_zinv_phys<T, NZ><<<zigrid(), thr_zi, sm_zi, s>>>(k1, (const C2*)b.B, (T*)u, twz(b.tw), b.err);
+        k_zinv_phys<T, NZ><<<zigrid(), thr_zi, sm_zi, s>>>(k1, (const C2*)b.B + 3 * BS, (T*)w, twz(b.tw), b.err);
         return cudaGetLastError();
     }
 

@@ -61,8 +61,8 @@
 #ifndef PS_ZWS
 #define PS_ZWS 1
 #endif
-// lines per block of the physical <-> z-spectral kernels: shared-memory
-// budget in KiB for twice their tiles
+// lines per block of the one-field physical inverse (k_zinv_sub): shared-
+// memory budget in KiB for twice their tiles
 #ifndef PS_LY_SMEM_KB
 #define PS_LY_SMEM_KB 64
 #endif
@@ -229,6 +229,39 @@ template <typename T, int N> struct Geo {
 };
 
 __device__ __forceinline__ int zaddr(int p, int line, int LP) { return line * LP + p + (p >> 4); }
+
+// Physical <-> z-spectral transforms (k_zinv_phys, k_zfwd_phys): persistent
+// blocks over batches of L lines (L even, dividing n^2), three thread groups
+// of G threads per line pair, one transform each: (u_x + i u_y) of either
+// line and (u_z[2m] + i u_z[2m + 1]). A batch's three fields come by bulk
+// copies into one of two staging buffers (spectral: L Kzp complex per field;
+// physical: L N reals per field). L is the batch that puts the most threads
+// on an SM within the shared memory.
+template <typename T, int N> struct ZPhys {
+    using C2 = cplx<T>;
+    static constexpr int G = LineFFT<T, N, 1>::G;
+    static constexpr int LP = N + N / 16;
+    static constexpr int KZP = Geo<T, N>::KZP;
+    static constexpr int TWN = Geo<T, N>::tw_n;
+    static constexpr int smem(int l, bool fwd) {
+        const int stage = fwd ? 2 * 3 * l * N * (int)sizeof(T) : 2 * 3 * l * KZP * (int)sizeof(C2);
+        return stage + (int)sizeof(C2) * (3 * (l / 2) * LP + TWN) + 128;
+    }
+    static constexpr int threads(int l) { return 3 * (l / 2) * G; }
+    static constexpr int resident(int l, bool fwd) {   // threads per SM
+        int b = (227 * 1024) / (smem(l, fwd) + 1024);
+        if (b * threads(l) > 2048) b = 2048 / threads(l);
+        if (b > 32) b = 32;
+        return b * threads(l);
+    }
+    static constexpr int pick(bool fwd) {
+        int best = 2;
+        for (int l = 4; l <= 8; l *= 2)
+            if (threads(l) <= 512 && resident(l, fwd) >= resident(best, fwd)) best = l;
+        return best;
+    }
+    static constexpr int LI = pick(false), LF = pick(true);
+};
 
 // Dynamic shared memory rounded up to a 128-byte boundary (TMA destinations
 // need it; kernels reserve 128 bytes of slack). The extern array's own
@@ -1485,130 +1518,223 @@ k_xfwd_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUten
 }
 
 // ----------------------------------------------- physical <-> z-spectral
-// LY z lines per block, G threads per line (one warp or less: warp barriers
-// between FFT stages). Template N is the z-line length (nz); there are
-// kp.n^2 lines. Each line's (u_x + i u_y) is one complex transform;
-// u_z of lines 2m and 2m + 1 share one, (u_z[2m] + i u_z[2m+1]).
-// Forward: physical u (3 x n^3 real) -> B fields 0..2 (z r2c, kz < Kz).
+// Persistent blocks over batches of L z lines (ZPhys): the batch's three
+// fields arrive by bulk copies into one of two staging buffers while the
+// block transforms the previous batch. Thread group r of line pair m (3 per
+// pair, G threads each) runs one transform: r = 0, 1 the (u_x + i u_y) of
+// line 2m + r, r = 2 the (u_z[2m] + i u_z[2m+1]). Template N is the z-line
+// length (nz); there are kp.n^2 lines, a multiple of L. Every mbarrier wait
+// is bounded: on timeout the kernel sets *err and stops.
+//
+// Forward: physical u (3 x n^3 real, [x][y][z]) -> B fields 0..2 (z r2c,
+// kz < Kz).
 template <typename T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
-k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg) {
+__global__ void __launch_bounds__(ZPhys<T, N>::threads(ZPhys<T, N>::LF))
+k_zfwd_phys(KP kp, const T* __restrict__ u, cplx<T>* __restrict__ B, const cplx<T>* __restrict__ twg,
+            int* __restrict__ err) {
     using C2 = cplx<T>;
-    using GE = Geo<T, N>;
-    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
-    static_assert(LY % 2 == 0, "z lines come in pairs");
+    using ZP = ZPhys<T, N>;
+    constexpr int G = ZP::G, L = ZP::LF, LP = ZP::LP;
     constexpr bool WS = G <= 32 && 32 % G == 0;
     using FFT = LineFFT<T, N, -1, WS>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* t0 = tw + GE::tw_n;          // [LY][LP]: (u_x + i u_y) of each line
-    C2* t1 = t0 + LY * LP;           // [LY / 2][LP]: u_z of each line pair
-    const int line = threadIdx.x / G, g = threadIdx.x % G;
-    const long lid = (long)blockIdx.x * LY + line;
+    T* stage = reinterpret_cast<T*>(smem_base128(smraw));   // [2][3][L][N]
+    if ((smem_u32(stage) & 127u) || (reinterpret_cast<uintptr_t>(u) & 15u)) {   // never expected
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* tiles = reinterpret_cast<C2*>(stage + 2 * 3 * L * N);   // [3 L / 2][LP]
+    C2* tw = tiles + 3 * (L / 2) * LP;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int grp = threadIdx.x / G, g = threadIdx.x % G;
+    const int m = grp / 3, r = grp % 3;
     const int Kz = kp.Kz, Kzp = kp.Kzp;
-    const size_t BS = (size_t)kp.n * kp.n * Kzp;
-    const size_t lo = (size_t)lid * Kzp;
-    const size_t N3 = (size_t)kp.n * kp.n * N;
-    const size_t po = (size_t)lid * N;
-    load_tw(tw, twg, GE::tw_n);
-    __syncthreads();
-    {
-        const Pad16 addr{line * LP};
-        auto load = [&](int z) -> C2 { return cmk<C2>(u[po + z], u[N3 + po + z]); };
-        auto store = [&](int p, C2 v) { t0[addr(p)] = v; };
-        FFT::template run<false>(t0, tw, addr, g, load, store);
+    const long nlines = (long)kp.n * kp.n;
+    const int nb = (int)(nlines / L);
+    const size_t BS = (size_t)nlines * Kzp;
+    const size_t N3 = (size_t)nlines * N;
+    constexpr uint32_t fbytes = (uint32_t)(L * N * sizeof(T));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
     }
-    {
-        const bool even = (line & 1) == 0;
-        const Pad16 addr{(line >> 1) * LP};
-        auto load = [&](int z) -> C2 { return cmk<C2>(u[2 * N3 + po + z], u[2 * N3 + po + N + z]); };
-        auto store = [&](int p, C2 v) { t1[addr(p)] = v; };
-        FFT::template run_masked<false>(t1, tw, addr, g, load, store, even);
-    }
+    load_tw(tw, twg, ZP::TWN);
     __syncthreads();
-    C2* o0 = B + lo;
-    C2* o1 = B + BS + lo;
-    C2* o2 = B + 2 * BS + lo;
-    const C2* w1 = t1 + (line >> 1) * LP;
-    for (int k = g; k < Kz; k += G) {
-        const int m = (N - k) % N;
-        const C2 zk = t0[zaddr(k, line, LP)];
-        const C2 zm = t0[zaddr(m, line, LP)];
-        // P = (Z_k + conj Z_{-k}) / 2,  Q = (Z_k - conj Z_{-k}) / (2 i)
-        o0[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-        o1[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
-        const C2 wk = w1[k + (k >> 4)], wm = w1[m + (m >> 4)];
-        o2[k] = (line & 1) ? cmk<C2>((T)0.5 * (wk.y + wm.y), (T)0.5 * (wm.x - wk.x))
-                           : cmk<C2>((T)0.5 * (wk.x + wm.x), (T)0.5 * (wk.y - wm.y));
+    auto issue = [&](int b, int buf) {  // one thread
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], 3 * fbytes);
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f)
+            bulk_g2s(stage + (size_t)(buf * 3 + f) * L * N, u + f * N3 + (size_t)b * L * N, fbytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < nb) issue(blockIdx.x, 0);
+    C2* t = tiles + (size_t)grp * LP;
+    const Pad16 addr{grp * LP};
+    int it = 0;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = b + (int)gridDim.x < nb;
+        // the other buffer was read by the previous batch (end-of-batch barrier)
+        if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const T* st = stage + (size_t)buf * 3 * L * N;
+        // r < 2: fields 0, 1 of line 2m + r; r = 2: field 2 of lines 2m, 2m + 1
+        const T* s0 = r < 2 ? st + (size_t)(2 * m + r) * N : st + (size_t)(2 * L + 2 * m) * N;
+        const T* s1 = r < 2 ? s0 + (size_t)L * N : s0 + N;
+        auto load = [&](int z) -> C2 { return cmk<C2>(s0[z], s1[z]); };
+        FFT::template run_tile<false>(tiles, tw, addr, g, load);
+        // the transform's outputs are read back by other threads of the group
+        if constexpr (WS) __syncwarp(warp_lanes());
+        else __syncthreads();
+        const size_t lo = ((size_t)b * L + 2 * m + (r == 1)) * Kzp;
+        C2* oP = r < 2 ? B + lo : B + 2 * BS + lo;              // P = (Z_k + conj Z_{-k}) / 2
+        C2* oQ = r < 2 ? B + BS + lo : B + 2 * BS + lo + Kzp;   // Q = (Z_k - conj Z_{-k}) / (2 i)
+        for (int k = g; k < Kz; k += G) {
+            const int mk = (N - k) % N;
+            const C2 zk = t[k + (k >> 4)], zm = t[mk + (mk >> 4)];
+            oP[k] = cmk<C2>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            oQ[k] = cmk<C2>((T)0.5 * (zk.y + zm.y), (T)0.5 * (zm.x - zk.x));
+        }
+        __syncthreads();
     }
 }
 
 // Inverse: B fields 0..2 (z spectral, kz < Kz) -> physical u (3 x n^3 real).
-// MODE 1: one field, B field 0 -> u[0..n^3) as u := (inverse) - u, each
-// thread group on a pair of lines (launch (zblocks() + 1) / 2 blocks).
-template <typename T, int N, int MODE = 0>
+template <typename T, int N>
+__global__ void __launch_bounds__(ZPhys<T, N>::threads(ZPhys<T, N>::LI))
+k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg,
+            int* __restrict__ err) {
+    using C2 = cplx<T>;
+    using ZP = ZPhys<T, N>;
+    constexpr int G = ZP::G, L = ZP::LI, LP = ZP::LP, KZP = ZP::KZP;
+    constexpr bool WS = G <= 32 && 32 % G == 0;
+    using FFT = LineFFT<T, N, 1, WS>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][3][L][KZP]
+    if (smem_u32(stage) & 127u) {   // never expected
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* tiles = stage + 2 * 3 * L * KZP;   // [3 L / 2][LP]
+    C2* tw = tiles + 3 * (L / 2) * LP;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int grp = threadIdx.x / G, g = threadIdx.x % G;
+    const int m = grp / 3, r = grp % 3;
+    const int Kz = kp.Kz, Kzp = kp.Kzp;
+    const long nlines = (long)kp.n * kp.n;
+    const int nb = (int)(nlines / L);
+    const size_t BS = (size_t)nlines * Kzp;
+    const size_t N3 = (size_t)nlines * N;
+    const uint32_t fbytes = (uint32_t)(L * Kzp * sizeof(C2));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, ZP::TWN);
+    __syncthreads();
+    auto issue = [&](int b, int buf) {  // one thread
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], 3 * fbytes);
+#pragma unroll 1
+        for (int f = 0; f < 3; ++f)
+            bulk_g2s(stage + (size_t)(buf * 3 + f) * L * KZP, B + f * BS + (size_t)b * L * Kzp, fbytes, &bar[buf]);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < nb) issue(blockIdx.x, 0);
+    const Pad16 addr{grp * LP};
+    int it = 0;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = b + (int)gridDim.x < nb;
+        if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const C2* st = stage + (size_t)buf * 3 * L * KZP;
+        // r < 2: (A + i B) of fields 0, 1 of line 2m + r; r = 2: of field 2
+        // of lines 2m and 2m + 1
+        const C2* fa = r < 2 ? st + (size_t)(2 * m + r) * Kzp : st + (size_t)2 * L * KZP + (size_t)(2 * m) * Kzp;
+        const C2* fb = r < 2 ? fa + (size_t)L * KZP : fa + Kzp;
+        auto load = [&](int q) -> C2 {
+            if (q < Kz) {
+                C2 a = fa[q], c = fb[q];
+                if (q == 0) { a.y = 0; c.y = 0; }
+                return cmk<C2>(a.x - c.y, a.y + c.x);
+            }
+            if (q > N - Kz) {
+                const C2 a = fa[N - q], c = fb[N - q];
+                return cmk<C2>(a.x + c.y, c.x - a.y);
+            }
+            return cmk<C2>((T)0, (T)0);
+        };
+        const size_t po = ((size_t)b * L + 2 * m + (r == 1)) * N;
+        T* o0 = r < 2 ? u + po : u + 2 * N3 + po;
+        T* o1 = r < 2 ? u + N3 + po : u + 2 * N3 + po + N;
+        auto store = [&](int z, C2 v) {
+            o0[z] = v.x;
+            o1[z] = v.y;
+        };
+        FFT::template run<false>(tiles, tw, addr, g, load, store);
+        // the staging buffer and the tiles are reused by the next batches
+        __syncthreads();
+    }
+}
+
+// One field, B field 0 (z spectral) -> u[0..n^3) as u := (inverse) - u;
+// LY lines per block, each thread group on a pair of lines (launch
+// (n^2 / LY + 1) / 2 blocks).
+template <typename T, int N>
 __global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
-k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
+k_zinv_sub(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
     using C2 = cplx<T>;
     using GE = Geo<T, N>;
     constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
-    static_assert(LY % 2 == 0, "z lines come in pairs");
     constexpr bool WS = G <= 32 && 32 % G == 0;
     using FFT = LineFFT<T, N, 1, WS>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* tiles = tw + GE::tw_n;       // [LY][LP], reused by the two transforms
+    C2* tiles = tw + GE::tw_n;       // [LY][LP]
     const int line = threadIdx.x / G, g = threadIdx.x % G;
     const long lid = (long)blockIdx.x * LY + line;
     const int Kz = kp.Kz, Kzp = kp.Kzp;
-    const size_t BS = (size_t)kp.n * kp.n * Kzp;
-    const size_t lo = (size_t)lid * Kzp;
-    const size_t N3 = (size_t)kp.n * kp.n * N;
-    const size_t po = (size_t)lid * N;
     load_tw(tw, twg, GE::tw_n);
     const Pad16 addr{line * LP};
     __syncthreads();
-    // (A + i B) of two real lines from their half spectra a, b
-    auto two = [&](const C2* fa, const C2* fb, int q) -> C2 {
+    const bool on = 2 * lid < (long)kp.n * kp.n;
+    const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
+    const C2* fa = B + lo2;
+    const C2* fb = fa + Kzp;
+    // (A + i B) of the two real lines from their half spectra
+    auto load = [&](int q) -> C2 {
         if (q < Kz) {
-            C2 a = fa[q], b = fb[q];
-            if (q == 0) { a.y = 0; b.y = 0; }
-            return cmk<C2>(a.x - b.y, a.y + b.x);
+            C2 a = fa[q], c = fb[q];
+            if (q == 0) { a.y = 0; c.y = 0; }
+            return cmk<C2>(a.x - c.y, a.y + c.x);
         }
         if (q > N - Kz) {
-            const C2 a = fa[N - q], b = fb[N - q];
-            return cmk<C2>(a.x + b.y, b.x - a.y);
+            const C2 a = fa[N - q], c = fb[N - q];
+            return cmk<C2>(a.x + c.y, c.x - a.y);
         }
         return cmk<C2>((T)0, (T)0);
     };
-    if constexpr (MODE == 1) {
-        // one field: thread group `line` takes the line pair (2 lid, 2 lid + 1)
-        // (launched with half the blocks, rounded up)
-        const bool on = 2 * lid < (long)kp.n * kp.n;
-        const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
-        const C2* f0 = B + lo2;
-        auto load = [&](int q) -> C2 { return two(f0, f0 + Kzp, q); };
-        auto store = [&](int z, C2 v) {
-            u[po2 + z] = v.x - u[po2 + z];
-            u[po2 + N + z] = v.y - u[po2 + N + z];
-        };
-        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, on);
-        return;
-    }
-    {
-        auto load = [&](int q) -> C2 { return two(B + lo, B + BS + lo, q); };
-        auto store = [&](int z, C2 v) { u[po + z] = v.x; u[N3 + po + z] = v.y; };
-        FFT::template run<false>(tiles, tw, addr, g, load, store);
-    }
-    // the tile is reused: every thread of the line is past the last stage
-    if constexpr (WS) __syncwarp(warp_lanes());
-    else __syncthreads();
-    {
-        const C2* f2 = B + 2 * BS + lo;
-        auto load = [&](int q) -> C2 { return two(f2, f2 + Kzp, q); };
-        auto store = [&](int z, C2 v) { u[2 * N3 + po + z] = v.x; u[2 * N3 + po + N + z] = v.y; };
-        FFT::template run_masked<false>(tiles, tw, addr, g, load, store, (line & 1) == 0);
-    }
+    auto store = [&](int z, C2 v) {
+        u[po2 + z] = v.x - u[po2 + z];
+        u[po2 + N + z] = v.y - u[po2 + N + z];
+    };
+    FFT::template run_masked<false>(tiles, tw, addr, g, load, store, on);
 }
 
 }  // namespace ps
