@@ -34,9 +34,14 @@ def test_step_flop_model():
 
 
 def test_traffic_figure_tracks_kernel_sources(monkeypatch):
-    got = bench.measured_traffic("z_c2r_nonlinear_r2c", 768)
-    assert got is None or got > 1e10
-    assert bench.measured_traffic("no_such_kernel", 768) is None
+    # the figure is scaled by grid points: ~10.5 GB per 768^3 z pass
+    npts = 768 ** 3
+    got = bench.measured_traffic("z_c2r_nonlinear_r2c", npts)
+    assert got is None or 1e10 < got < 1.2e10
+    assert bench.measured_traffic("no_such_kernel", npts) is None
+    # a figure taken on other kernel sources is not used
+    monkeypatch.setattr(bench, "sources_sha256", lambda: "0" * 64)
+    assert bench.measured_traffic("z_c2r_nonlinear_r2c", npts) is None
 
 
 def _worker(rank, world, port, out):
