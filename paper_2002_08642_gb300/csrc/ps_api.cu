@@ -409,11 +409,11 @@ cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag,
         if ((e = cudaMemsetAsync(chi, 0, n3 * sizeof(T), s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(us, 0, 3 * n3 * sizeof(T), s)) != cudaSuccess) return e;
     }
-    if ((e = cudaMemsetAsync(flag, 0, n * n, s)) != cudaSuccess) return e;
-    k_mask_clear<<<1216, 256, 0, s>>>(m, par, chi, us, sizeof(T), n3);
+    // the previous call's points, the line flags, the other list's count
+    // and the node positions
     const int np = par ^ 1;
-    if ((e = cudaMemsetAsync(m.cnt + np, 0, 8, s)) != cudaSuccess) return e;
-    k_mask_nodes<<<(a.n_nodes + 127) / 128, 128, 0, s>>>(m, a);
+    const int cb = (a.n_nodes + 255) / 256 > 1216 ? (a.n_nodes + 255) / 256 : 1216;
+    k_mask_clear<T><<<cb, 256, 0, s>>>(m, a, par, (T*)chi, (T*)us, flag, n3, n * n);
     if (a.profile == PS_MASK_TANH) {
         k_mask_dense<T><<<2432, 128, 0, s>>>(m, a, (T*)chi, (T*)us, flag);
         *par_out = np;  // both lists empty: the next call must clear densely
@@ -422,7 +422,7 @@ cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag,
     k_mask_tris<T><<<a.n_tri > 0 ? (a.n_tri + 127) / 128 : 1, 128, 0, s>>>(m, a, a.tw + a.h);
     k_mask_prefix<<<1, 1024, 0, s>>>(m, a);
     k_mask_scatter1<T><<<2432, 256, 0, s>>>(m, a, np);
-    k_mask_scatter2<T><<<2432, 256, 0, s>>>(m, a);
+    if constexpr (sizeof(T) == 8) k_mask_scatter2<T><<<2432, 256, 0, s>>>(m, a);
     k_mask_eval<T><<<1216, 256, 0, s>>>(m, a, np, (T*)chi, (T*)us, flag);
     *par_out = np;
     return cudaGetLastError();

@@ -11,18 +11,21 @@
 //
 // Banded (cosine) profile, per call:
 //   clear     zero chi/u_s and reset the per-point keys of the points the
-//             previous call touched (list kept in the workspace);
-//   nodes     global node positions X_O + R x^(w) (double);
+//             previous call touched (list kept in the workspace), clear the
+//             line flags, and the global node positions X_O + R x^(w)
+//             (double);
 //   tris      per triangle (one thread each): grid-index bounding box and
 //             the geometry the pair tests need, in the context precision:
 //             vertex a as grid cell + offset, edges b - a and c - a;
 //   prefix    exclusive prefix sum of the box point counts (one block);
 //   scatter1  for every (triangle, box point) pair with distance < reach:
-//             atomicMin of the distance bits (non-negative IEEE values order
-//             like their bit patterns); the first writer appends the point
-//             to the touched list;
-//   scatter2  pairs whose distance equals the minimum bit for bit:
-//             atomicMin of the triangle index (ties -> smallest index);
+//             atomicMin of a 64-bit key (non-negative IEEE values order like
+//             their bit patterns); the first writer appends the point to the
+//             touched list. FP32: the key is the distance bits above the
+//             triangle index, so its minimum also names the winner (exact
+//             ties -> smallest index). FP64: the distance bits alone, and
+//   scatter2  (FP64 only) pairs within a few ulps of the minimum: atomicMin
+//             of the triangle index (near-ties -> smallest index);
 //   evaluate  per touched point: distance and barycentrics recomputed in
 //             double on the winning triangle, chi, u_s, line flags.
 // The distance used to pick the winner is computed in the context precision.
@@ -155,31 +158,34 @@ template <> struct KeyBits<double> {
     static __device__ __forceinline__ double val(unsigned long long k) { return __longlong_as_double((long long)k); }
 };
 
-__global__ void k_mask_clear(MaskWs m, int par, void* chi, void* us, size_t elem, size_t n3) {
+// First kernel of a call: zero chi/u_s and reset the key and winner of the
+// points the previous call touched (list `par`), clear the line flags
+// (n^2 bytes, 16-byte aligned), reset the other list's count, and the
+// global node positions X_O + R x^(w) (double).
+template <typename T>
+__global__ void k_mask_clear(MaskWs m, MaskArgs a, int par, T* chi, T* us, uint8_t* flag, size_t n3, size_t nflag) {
+    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+    if (tid == 0) m.cnt[par ^ 1] = 0;
+    if (tid < (unsigned long long)a.n_nodes) {
+        const int i = (int)tid;
+        for (int r = 0; r < 3; ++r) {
+            double s = a.XO[r];
+            for (int c = 0; c < 3; ++c) s += a.R[3 * r + c] * a.xw[3 * i + c];
+            m.xg[3 * i + r] = s;
+        }
+    }
+    uint4* f4 = reinterpret_cast<uint4*>(flag);
+    for (unsigned long long i = tid; i < nflag / 16; i += nth) f4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid < nflag % 16) flag[nflag / 16 * 16 + tid] = 0;
     const unsigned long long cnt = m.cnt[par];
     const uint32_t* L = m.list[par];
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long i = tid; i < cnt; i += nth) {
         const uint32_t p = L[i];
         m.key[p] = ~0ull;
         m.win[p] = 0x7fffffff;
-        if (elem == 4) {
-            ((float*)chi)[p] = 0.f;
-            for (int c = 0; c < 3; ++c) ((float*)us)[c * n3 + p] = 0.f;
-        } else {
-            ((double*)chi)[p] = 0.0;
-            for (int c = 0; c < 3; ++c) ((double*)us)[c * n3 + p] = 0.0;
-        }
-    }
-}
-
-__global__ void k_mask_nodes(MaskWs m, MaskArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_nodes) return;
-    for (int r = 0; r < 3; ++r) {
-        double s = a.XO[r];
-        for (int c = 0; c < 3; ++c) s += a.R[3 * r + c] * a.xw[3 * i + c];
-        m.xg[3 * i + r] = s;
+        chi[p] = (T)0;
+        for (int c = 0; c < 3; ++c) us[c * n3 + p] = (T)0;
     }
 }
 
@@ -309,7 +315,12 @@ __global__ void k_mask_scatter1(MaskWs m, MaskArgs a, int par) {
         uint32_t p;
         T d;
         if (!pair_dist<T>(m, a, t, w - m.pre[t], &p, &d)) continue;
-        const unsigned long long old = atomicMin(&m.key[p], KeyBits<T>::of(d));
+        // FP32: distance bits above the triangle index, so the minimum key
+        // also holds the winner (exact ties -> smallest index); FP64: the
+        // distance alone, the winner by k_mask_scatter2
+        unsigned long long key = KeyBits<T>::of(d);
+        if constexpr (sizeof(T) == 4) key = (key << 32) | (unsigned long long)(uint32_t)t;
+        const unsigned long long old = atomicMin(&m.key[p], key);
         if (old == ~0ull) {
             const unsigned long long slot = atomicAdd(&m.cnt[par], 1ull);
             m.list[par][slot] = p;
@@ -388,7 +399,13 @@ __global__ void k_mask_eval(MaskWs m, MaskArgs a, int par, T* chi, T* us, uint8_
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = m.list[par][i];
-        const int t = m.win[p];
+        int t;
+        if constexpr (sizeof(T) == 4) {   // the winner is the key's low word; kept for the VJP
+            t = (int)(uint32_t)m.key[p];
+            m.win[p] = t;
+        } else {
+            t = m.win[p];
+        }
         if (t >= 0 && t < a.n_tri) eval_point<T>(m, a, p, t, chi, us, flag);
     }
 }
