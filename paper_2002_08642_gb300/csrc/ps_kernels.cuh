@@ -174,9 +174,14 @@ template <typename T, int N> struct Geo {
     static constexpr int zsmem(int l) {
         return (int)sizeof(C2) * (ZNB * 6 * l * KZP + 3 * l * LP + tw_count(N) + 1) + 128;
     }
+    // lines of at most 16 threads take batches of 2 lines (measured on GB300:
+    // 256^3 z pass 0.187 -> 0.177 ms); longer lines the largest batch within
+    // the thread and shared-memory budgets (384^3: 0.611 ms against 0.652 ms
+    // with 2 lines)
     static constexpr int lz_pick() {
+        const int maxthr = G <= 16 ? 6 * G : PS_ZP_MAXTHR;
         int l = 2;
-        while (3 * (2 * l) * G <= PS_ZP_MAXTHR && zsmem(2 * l) <= PS_ZP_SMEM_KB * 1024 && (N * N) % (2 * l) == 0)
+        while (3 * (2 * l) * G <= maxthr && zsmem(2 * l) <= PS_ZP_SMEM_KB * 1024 && (N * N) % (2 * l) == 0)
             l *= 2;
         return l;
     }
