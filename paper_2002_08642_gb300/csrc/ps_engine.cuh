@@ -35,7 +35,7 @@ struct Bufs {
 static constexpr int kEvPerStep = 10;
 
 struct Ops {
-    int n, nz, C, C5, LY, G;
+    int n, nz, C, C5, G;
     int cy2, br2, cy4, br4;   // TMA box widths (complex) and heights of the y passes
     int cx1, cx5;             // TMA box widths of the x passes (heights br2, br4)
     int zblocks;  // blocks of the z pass (= number of force partials), set by prepare
@@ -73,11 +73,9 @@ template <typename T, int N, int NZ = N> struct Engine {
     static constexpr size_t tw_bytes = (size_t)GE::tw_n * sizeof(C2);
     static constexpr size_t sm_strided = tw_bytes + (size_t)N * GE::C * sizeof(C2);
     static constexpr size_t sm_x5 = tw_bytes + (size_t)3 * N * GE::C5 * sizeof(C2);
-    static constexpr size_t sm_z = (size_t)GZ::tw_n * sizeof(C2) + (size_t)3 * GZ::LY * GZ::LP * sizeof(C2) / 2;
     static constexpr size_t sm_zp = (size_t)GZ::zsmem(GZ::LZ);
     static constexpr int thr_s = GE::C * GE::G;
     static constexpr int thr_5 = GE::C5 * GE::G;
-    static constexpr int thr_z = GZ::LY * GZ::G;
     static constexpr int thr_zp = 3 * GZ::LZ * GZ::G;
     // persistent physical <-> z-spectral transforms
     using ZP = ZPhys<T, NZ>;
@@ -85,12 +83,19 @@ template <typename T, int N, int NZ = N> struct Engine {
     static constexpr size_t sm_zf = (size_t)ZP::smem(ZP::LF, true);
     static constexpr int thr_zi = ZP::threads(ZP::LI);
     static constexpr int thr_zf = ZP::threads(ZP::LF);
-    static_assert((N * N) % ZP::LI == 0 && (N * N) % ZP::LF == 0, "z-line batches divide the lines");
+    static constexpr size_t sm_zs = (size_t)ZP::smem_sub(ZP::LS);
+    static constexpr int thr_zs = ZP::threads_sub(ZP::LS);
+    static_assert((N * N) % ZP::LI == 0 && (N * N) % ZP::LF == 0 && (N * N) % ZP::LS == 0,
+                  "z-line batches divide the lines");
     static int& zigrid() {
         static int g = 0;
         return g;
     }
     static int& zfgrid() {
+        static int g = 0;
+        return g;
+    }
+    static int& zsgrid() {
         static int g = 0;
         return g;
     }
@@ -148,7 +153,7 @@ template <typename T, int N, int NZ = N> struct Engine {
         if ((e = attr(k_zpass<T, NZ, true, false, N>, sm_zp))) return e;
         if ((e = attr(k_xinv<T, N, 1>, sm_strided))) return e;
         if ((e = attr(k_yinv<T, N, 1>, sm_strided))) return e;
-        if ((e = attr(k_zinv_sub<T, NZ>, sm_z))) return e;
+        if ((e = attr(k_zinv_sub<T, NZ>, sm_zs))) return e;
         if ((e = attr(k_zfwd_phys<T, NZ>, sm_zf))) return e;
         if ((e = attr(k_zinv_phys<T, NZ>, sm_zi))) return e;
         if ((e = attr(k_xfwd<T, N, 0>, sm_x5))) return e;
@@ -189,12 +194,13 @@ template <typename T, int N, int NZ = N> struct Engine {
         zigrid() = nsm * (occ < 1 ? 1 : occ);
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zfwd_phys<T, NZ>, thr_zf, sm_zf))) return e;
         zfgrid() = nsm * (occ < 1 ? 1 : occ);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zinv_sub<T, NZ>, thr_zs, sm_zs))) return e;
+        zsgrid() = nsm * (occ < 1 ? 1 : occ);
         return cudaSuccess;
     }
 
     static dim3 grid_xs(const KP& kp, int C) { return dim3(kp.Kzp / C, kp.K); }
     static dim3 grid_ys(const KP& kp) { return dim3(kp.Kzp / GE::C, N); }
-    static int zblocks() { return N * N / GZ::LY; }
 
 
     // resume: B already holds u and omega of the state (y-inverse output,
@@ -308,7 +314,7 @@ template <typename T, int N, int NZ = N> struct Engine {
                                                             (const T*)b.Ex, (const T*)b.Ez, 0, tw, b.err);
         k_xinv<T, N, 1><<<grid_xs(k1, GE::C), thr_s, sm_strided, s>>>(k1, pih, (C2*)b.A, tw);
         k_yinv_tma<T, N, 1, KZ_><<<y2grid(), thr_y2, sm_y2, s>>>(*b.tmA, k1, nout, tw, b.err);
-        k_zinv_sub<T, NZ><<<(zblocks() + 1) / 2, thr_z, sm_z, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw));
+        k_zinv_sub<T, NZ><<<zsgrid(), thr_zs, sm_zs, s>>>(k1, (const C2*)nout, (T*)p, twz(b.tw), b.err);
         return cudaGetLastError();
     }
 
@@ -345,7 +351,7 @@ template <typename T, int N, int NZ = N> struct Engine {
 
     static Ops ops() {
         Ops o;
-        o.n = N; o.nz = NZ; o.C = GE::C; o.C5 = GE::C5; o.LY = GE::LY; o.G = GE::G;
+        o.n = N; o.nz = NZ; o.C = GE::C; o.C5 = GE::C5; o.G = GE::G;
         o.cy2 = GE::CY2; o.br2 = GE::brows(GE::K); o.cy4 = GE::CY4; o.br4 = GE::brows(N);
         o.cx1 = GE::CX1; o.cx5 = GE::CX5;
         o.zblocks = 0;

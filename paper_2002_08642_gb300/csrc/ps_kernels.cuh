@@ -61,11 +61,6 @@
 #ifndef PS_ZWS
 #define PS_ZWS 1
 #endif
-// lines per block of the one-field physical inverse (k_zinv_sub): shared-
-// memory budget in KiB for twice their tiles
-#ifndef PS_LY_SMEM_KB
-#define PS_LY_SMEM_KB 64
-#endif
 // tile width of the TMA-staged y passes (0 = automatic)
 #ifndef PS_TY_C
 #define PS_TY_C 0
@@ -146,8 +141,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* out, double* 
 }
 
 // Launch geometry per (T, n): tile width C of the strided passes (128-byte
-// rows), C5 of the x-forward/update pass (three tiles must fit), LY lines
-// per block of the z pass.
+// rows), C5 of the x-forward/update pass (three tiles must fit), the z
+// pass's lines per batch and the TMA passes' tile widths.
 template <typename T, int N> struct Geo {
     using C2 = cplx<T>;
     static constexpr int G = LineFFT<T, N, 1>::G;
@@ -156,15 +151,6 @@ template <typename T, int N> struct Geo {
     static constexpr int C5 = (3 * N * CW * (int)sizeof(C2) <= 110 * 1024) ? CW
                             : (3 * N * (CW / 2) * (int)sizeof(C2) <= 150 * 1024) ? CW / 2 : CW / 4;
     static constexpr int LP = N + N / 16;                  // padded z line
-    static constexpr int ly_threads() { int l = 256 / G; return l < 1 ? 1 : l; }
-    static constexpr int ly_smem() {
-        int l = 1;
-        while (l * 2 * 3 * LP * (int)sizeof(C2) <= PS_LY_SMEM_KB * 1024) l *= 2;
-        return l;
-    }
-    static constexpr int LYa = ly_threads() < ly_smem() ? ly_threads() : ly_smem();
-    static constexpr int ly_fix(int l) { while (l > 1 && (N * N) % l != 0) l /= 2; return l; }
-    static constexpr int LY = ly_fix(LYa) < 2 ? 2 : ly_fix(LYa);   // even: z lines are paired
     // kept z modes, padded to the tile width
     static constexpr int KZ = (N - 1) / 3 + 1;
     static constexpr int KZP = (KZ + CW - 1) / CW * CW;
@@ -266,6 +252,25 @@ template <typename T, int N> struct ZPhys {
         return best;
     }
     static constexpr int LI = pick(false), LF = pick(true);
+    // k_zinv_sub: one field, one thread group per line pair; a batch stages
+    // its L spectral lines and its L physical lines of u
+    static constexpr int smem_sub(int l) {
+        return 2 * l * (KZP * (int)sizeof(C2) + N * (int)sizeof(T)) + (int)sizeof(C2) * ((l / 2) * LP + TWN) + 128;
+    }
+    static constexpr int threads_sub(int l) { return (l / 2) * G; }
+    static constexpr int resident_sub(int l) {
+        int b = (227 * 1024) / (smem_sub(l) + 1024);
+        if (b * threads_sub(l) > 2048) b = 2048 / threads_sub(l);
+        if (b > 32) b = 32;
+        return b * threads_sub(l);
+    }
+    static constexpr int pick_sub() {
+        int best = 2;
+        for (int l = 4; l <= 16; l *= 2)
+            if (threads_sub(l) <= 512 && resident_sub(l) >= resident_sub(best)) best = l;
+        return best;
+    }
+    static constexpr int LS = pick_sub();
 };
 
 // Dynamic shared memory rounded up to a 128-byte boundary (TMA destinations
@@ -1698,48 +1703,89 @@ k_zinv_phys(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<
     }
 }
 
-// One field, B field 0 (z spectral) -> u[0..n^3) as u := (inverse) - u;
-// LY lines per block, each thread group on a pair of lines (launch
-// (n^2 / LY + 1) / 2 blocks).
+// One field, B field 0 (z spectral) -> u[0..n^3) as u := (inverse) - u:
+// persistent blocks over batches of L lines; a batch's L spectral lines and
+// its L lines of u arrive by bulk copies into one of two staging buffers;
+// thread group m (G threads) transforms the line pair (2m, 2m + 1) as one
+// complex line. Bounded waits: on timeout the kernel sets *err and stops.
 template <typename T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::LY * Geo<T, N>::G)
-k_zinv_sub(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg) {
+__global__ void __launch_bounds__(ZPhys<T, N>::threads_sub(ZPhys<T, N>::LS))
+k_zinv_sub(KP kp, const cplx<T>* __restrict__ B, T* __restrict__ u, const cplx<T>* __restrict__ twg,
+           int* __restrict__ err) {
     using C2 = cplx<T>;
-    using GE = Geo<T, N>;
-    constexpr int G = GE::G, LY = GE::LY, LP = GE::LP;
+    using ZP = ZPhys<T, N>;
+    constexpr int G = ZP::G, L = ZP::LS, LP = ZP::LP, KZP = ZP::KZP;
     constexpr bool WS = G <= 32 && 32 % G == 0;
     using FFT = LineFFT<T, N, 1, WS>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2* tw = reinterpret_cast<C2*>(smraw);
-    C2* tiles = tw + GE::tw_n;       // [LY][LP]
-    const int line = threadIdx.x / G, g = threadIdx.x % G;
-    const long lid = (long)blockIdx.x * LY + line;
+    C2* stage = reinterpret_cast<C2*>(smem_base128(smraw));   // [2][L][KZP] spectral
+    T* ustage = reinterpret_cast<T*>(stage + 2 * L * KZP);     // [2][L][N] physical
+    if ((smem_u32(stage) & 127u) || (reinterpret_cast<uintptr_t>(u) & 15u)) {   // never expected
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    C2* tiles = reinterpret_cast<C2*>(ustage + 2 * L * N);    // [L / 2][LP]
+    C2* tw = tiles + (L / 2) * LP;
+    __shared__ __align__(8) uint64_t bar[2];
+    const int m = threadIdx.x / G, g = threadIdx.x % G;
     const int Kz = kp.Kz, Kzp = kp.Kzp;
-    load_tw(tw, twg, GE::tw_n);
-    const Pad16 addr{line * LP};
+    const long nlines = (long)kp.n * kp.n;
+    const int nb = (int)(nlines / L);
+    const uint32_t sbytes = (uint32_t)(L * Kzp * sizeof(C2));
+    constexpr uint32_t ubytes = (uint32_t)(L * N * sizeof(T));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_tw(tw, twg, ZP::TWN);
     __syncthreads();
-    const bool on = 2 * lid < (long)kp.n * kp.n;
-    const size_t lo2 = (size_t)(2 * lid) * Kzp, po2 = (size_t)(2 * lid) * N;
-    const C2* fa = B + lo2;
-    const C2* fb = fa + Kzp;
-    // (A + i B) of the two real lines from their half spectra
-    auto load = [&](int q) -> C2 {
-        if (q < Kz) {
-            C2 a = fa[q], c = fb[q];
-            if (q == 0) { a.y = 0; c.y = 0; }
-            return cmk<C2>(a.x - c.y, a.y + c.x);
-        }
-        if (q > N - Kz) {
-            const C2 a = fa[N - q], c = fb[N - q];
-            return cmk<C2>(a.x + c.y, c.x - a.y);
-        }
-        return cmk<C2>((T)0, (T)0);
+    auto issue = [&](int b, int buf) {  // one thread
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[buf], sbytes + ubytes);
+        bulk_g2s(stage + (size_t)buf * L * KZP, B + (size_t)b * L * Kzp, sbytes, &bar[buf]);
+        bulk_g2s(ustage + (size_t)buf * L * N, u + (size_t)b * L * N, ubytes, &bar[buf]);
     };
-    auto store = [&](int z, C2 v) {
-        u[po2 + z] = v.x - u[po2 + z];
-        u[po2 + N + z] = v.y - u[po2 + N + z];
-    };
-    FFT::template run_masked<false>(tiles, tw, addr, g, load, store, on);
+    if (threadIdx.x == 0 && (int)blockIdx.x < nb) issue(blockIdx.x, 0);
+    const Pad16 addr{m * LP};
+    int it = 0;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const bool more = b + (int)gridDim.x < nb;
+        if (threadIdx.x == 0 && more) issue(b + gridDim.x, buf ^ 1);
+        const bool ok = mbar_wait(&bar[buf], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                if (more) mbar_wait(&bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const C2* fa = stage + (size_t)buf * L * KZP + (size_t)(2 * m) * Kzp;
+        const C2* fb = fa + Kzp;
+        const T* su = ustage + (size_t)buf * L * N + (size_t)(2 * m) * N;
+        // (A + i B) of the two real lines from their half spectra
+        auto load = [&](int q) -> C2 {
+            if (q < Kz) {
+                C2 a = fa[q], c = fb[q];
+                if (q == 0) { a.y = 0; c.y = 0; }
+                return cmk<C2>(a.x - c.y, a.y + c.x);
+            }
+            if (q > N - Kz) {
+                const C2 a = fa[N - q], c = fb[N - q];
+                return cmk<C2>(a.x + c.y, c.x - a.y);
+            }
+            return cmk<C2>((T)0, (T)0);
+        };
+        T* o = u + ((size_t)b * L + 2 * m) * N;
+        auto store = [&](int z, C2 v) {
+            o[z] = v.x - su[z];
+            o[N + z] = v.y - su[N + z];
+        };
+        FFT::template run<false>(tiles, tw, addr, g, load, store);
+        // the staging buffer and the tiles are reused by the next batches
+        __syncthreads();
+    }
 }
 
 }  // namespace ps
