@@ -36,10 +36,11 @@ __global__ void k_adj_spec1(KP kp, cplx<T>* __restrict__ lam, cplx<T>* __restric
     const size_t FS = (size_t)K * K * Kzp;
     const size_t tot = (size_t)K * K * Kz;
     const T dt = (T)kp.dt, s = (T)kp.ks, sz = (T)kp.ksz;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const int cz = (int)(i % Kz);
-        const size_t r = i / Kz;
-        const int cx = (int)(r % K), cy = (int)(r / K);
+    // 32-bit index arithmetic: K^2 Kz < 2^27 for every grid the library builds
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)tot; i += gridDim.x * blockDim.x) {
+        const int cz = (int)(i % (uint32_t)Kz);
+        const uint32_t r = i / (uint32_t)Kz;
+        const int cx = (int)(r % (uint32_t)K), cy = (int)(r / (uint32_t)K);
         const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
         const T E = Ex[cx] * Ex[cy] * Ez[cz];
         const T a1 = first ? dt * E : (T)1.5 * dt * E;
@@ -80,10 +81,11 @@ __global__ void k_adj_spec2(KP kp, cplx<T>* __restrict__ lam, const cplx<T>* __r
     const size_t tot = (size_t)K * K * Kz;
     const T s = (T)kp.ks, sz = (T)kp.ksz;
     const T n3 = (T)(1.0 / kp.invn3);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const int cz = (int)(i % Kz);
-        const size_t r = i / Kz;
-        const int cx = (int)(r % K), cy = (int)(r / K);
+    // 32-bit index arithmetic: K^2 Kz < 2^27 for every grid the library builds
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)tot; i += gridDim.x * blockDim.x) {
+        const int cz = (int)(i % (uint32_t)Kz);
+        const uint32_t r = i / (uint32_t)Kz;
+        const int cx = (int)(r % (uint32_t)K), cy = (int)(r / (uint32_t)K);
         const size_t o = ((size_t)cy * K + cx) * Kzp + cz;
         const T kx = s * (T)cmode_of(cx, mm, K), ky = s * (T)cmode_of(cy, mm, K), kz = sz * (T)cz;
         const C2 wx = Wb[o], wy = Wb[FS + o], wz = Wb[2 * FS + o];

@@ -437,7 +437,21 @@ template <typename T>
 static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* gus) {
     using C2 = cplx<T>;
     cudaStream_t s = c->stream;
-    const int nb = 4 * 152;
+    // grid-stride passes: exactly the blocks that are resident at once
+    static int spec1_blocks = 0, spec2_blocks = 0, pt_blocks = 0;
+    if (pt_blocks == 0) {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        if (nsm < 1) nsm = 1;
+        auto resident = [&](auto kern) {
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+            return (occ > 0 ? occ : 1) * nsm;
+        };
+        spec1_blocks = resident(k_adj_spec1<T>);
+        spec2_blocks = resident(k_adj_spec2<T>);
+        pt_blocks = resident(k_adj_point<T>);
+    }
     C2* lam = (C2*)c->adj_spec[0];
     C2* mu = (C2*)c->adj_spec[1];
     C2* G = (C2*)c->adj_spec[2];
@@ -447,22 +461,14 @@ static cudaError_t adjoint_step_t(ps_ctx* c, const AdjW& aw, void* gchi, void* g
     T* wp = (T*)c->adj_phys[1];
     T* np_ = (T*)c->adj_phys[2];
     cudaError_t e;
-    k_adj_spec1<T><<<nb, 256, 0, s>>>(c->kp, lam, mu, G, (const T*)c->b.Ex, (const T*)c->b.Ez, aw.first);
+    k_adj_spec1<T><<<spec1_blocks, 256, 0, s>>>(c->kp, lam, mu, G, (const T*)c->b.Ex, (const T*)c->b.Ez, aw.first);
     if ((e = c->ops->inv_uw(c->kp, c->b, up, wp, s)) != cudaSuccess) return e;
     if ((e = c->ops->inv_g(c->kp, c->b, np_, s)) != cudaSuccess) return e;
-    // grid-stride pointwise pass: exactly the blocks that are resident at once
-    static int pt_blocks = 0;
-    if (pt_blocks == 0) {
-        int occ = 0, nsm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adj_point<T>, 256, 0);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-        pt_blocks = (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
-    }
     k_adj_point<T><<<pt_blocks, 256, 0, s>>>(c->kp, aw, up, wp, np_, (const T*)c->b.chi, (const T*)c->b.us, (T*)gchi,
                                           (T*)gus);
     if ((e = c->ops->fwd3(c->kp, c->b, up, Ub, s)) != cudaSuccess) return e;
     if ((e = c->ops->fwd3(c->kp, c->b, wp, Wb, s)) != cudaSuccess) return e;
-    k_adj_spec2<T><<<nb, 256, 0, s>>>(c->kp, lam, Ub, Wb);
+    k_adj_spec2<T><<<spec2_blocks, 256, 0, s>>>(c->kp, lam, Ub, Wb);
     return cudaGetLastError();
 }
 
