@@ -394,6 +394,10 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Grid-stride launches of the rasteriser and its VJP are sized as multiples
+// of the GB300's 152 SMs (8 or 16 blocks per SM); any grid is correct.
+constexpr int kRasterSM = 152;
+
 template <typename T>
 cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag, unsigned char* ws, int par, bool init,
                           bool dense_dirty, cudaStream_t s, int* par_out) {
@@ -412,18 +416,18 @@ cudaError_t ps::rasterise(const MaskArgs& a, void* chi, void* us, uint8_t* flag,
     // the previous call's points, the line flags, the other list's count
     // and the node positions
     const int np = par ^ 1;
-    const int cb = (a.n_nodes + 255) / 256 > 1216 ? (a.n_nodes + 255) / 256 : 1216;
+    const int cb = (a.n_nodes + 255) / 256 > 8 * kRasterSM ? (a.n_nodes + 255) / 256 : 8 * kRasterSM;
     k_mask_clear<T><<<cb, 256, 0, s>>>(m, a, par, (T*)chi, (T*)us, flag, n3, n * n);
     if (a.profile == PS_MASK_TANH) {
-        k_mask_dense<T><<<2432, 128, 0, s>>>(m, a, (T*)chi, (T*)us, flag);
+        k_mask_dense<T><<<16 * kRasterSM, 128, 0, s>>>(m, a, (T*)chi, (T*)us, flag);
         *par_out = np;  // both lists empty: the next call must clear densely
         return cudaGetLastError();
     }
     k_mask_tris<T><<<a.n_tri > 0 ? (a.n_tri + 127) / 128 : 1, 128, 0, s>>>(m, a, a.tw + a.h);
     k_mask_prefix<<<1, 1024, 0, s>>>(m, a);
-    k_mask_scatter1<T><<<2432, 256, 0, s>>>(m, a, np);
-    if constexpr (sizeof(T) == 8) k_mask_scatter2<T><<<2432, 256, 0, s>>>(m, a);
-    k_mask_eval<T><<<1216, 256, 0, s>>>(m, a, np, (T*)chi, (T*)us, flag);
+    k_mask_scatter1<T><<<16 * kRasterSM, 256, 0, s>>>(m, a, np);
+    if constexpr (sizeof(T) == 8) k_mask_scatter2<T><<<16 * kRasterSM, 256, 0, s>>>(m, a);
+    k_mask_eval<T><<<8 * kRasterSM, 256, 0, s>>>(m, a, np, (T*)chi, (T*)us, flag);
     *par_out = np;
     return cudaGetLastError();
 }
@@ -995,11 +999,11 @@ ps_status ps_mask_nodes_vjp(ps_ctx* c, const void* grad_chi_dev, const void* gra
     if ((e = cudaMemsetAsync(c->gX, 0, (size_t)a.n_nodes * 3 * sizeof(double), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ps_mask_nodes_vjp");
     if (a.profile == PS_MASK_TANH) {
-        if (c->fp64) k_mask_vjp_dense<double><<<2432, 128, 0, c->stream>>>(m, a, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
-        else k_mask_vjp_dense<float><<<2432, 128, 0, c->stream>>>(m, a, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
+        if (c->fp64) k_mask_vjp_dense<double><<<16 * kRasterSM, 128, 0, c->stream>>>(m, a, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
+        else k_mask_vjp_dense<float><<<16 * kRasterSM, 128, 0, c->stream>>>(m, a, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
     } else {
-        if (c->fp64) k_mask_vjp_list<double><<<1216, 256, 0, c->stream>>>(m, a, c->mask_par, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
-        else k_mask_vjp_list<float><<<1216, 256, 0, c->stream>>>(m, a, c->mask_par, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
+        if (c->fp64) k_mask_vjp_list<double><<<8 * kRasterSM, 256, 0, c->stream>>>(m, a, c->mask_par, (const double*)grad_chi_dev, (const double*)grad_us_dev, (const double*)c->b.chi, c->gX);
+        else k_mask_vjp_list<float><<<8 * kRasterSM, 256, 0, c->stream>>>(m, a, c->mask_par, (const float*)grad_chi_dev, (const float*)grad_us_dev, (const float*)c->b.chi, c->gX);
     }
     k_vjp_to_wing<<<(a.n_nodes + 127) / 128, 128, 0, c->stream>>>(a, c->gX, grad_xw_dev);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ps_mask_nodes_vjp");
