@@ -453,8 +453,9 @@ def run_ours(args, cfg):
     peak, src = peaks()
     achieved = ab[top] / (tms / tl / 1e3) / 1e9
     step_bytes = sum(ab.values())
-    # five passes + rasteriser (clear, nodes, tris, prefix, scatter1, scatter2, eval)
-    kernels_per_step = 5 + 7
+    # five passes + rasteriser (clear with node positions, triangle boxes,
+    # prefix sum, pair pass, evaluate; FP64 adds a second pair pass)
+    kernels_per_step = 5 + (5 if cfg["precision"] == "fp32" else 6)
     # the z pass against the FP32 FMA rate: its line transforms (4.5 complex
     # length-n transforms per (x, y) line, 5 n log2 n FLOPs each) and the
     # pointwise term; it is bound by instruction issue, not by FMA throughput
