@@ -80,3 +80,29 @@ def test_reference_arm_prints_the_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_adjoint_bytes_model():
+    """The reversed step's byte model, kernel by kernel: each kernel reads and
+    writes whole arrays of four kinds (spectral state K^2 Kz, x-physical
+    n K Kz, z-spectral n^2 Kz complex; physical n^3 real). At 512^3 the
+    families are the totals of the per-kernel launch list (one reversed step:
+    two z c2r for u and omega, one for nbar, two forward passes)."""
+    n = 512
+    K, Kz = 341, 171
+    spec, xphys, zspec, phys = K * K * Kz * 8, n * K * Kz * 8, n * n * Kz * 8, n ** 3 * 4
+    xinv = lambda f_in, f_out: f_in * spec + f_out * xphys
+    yinv = lambda f: f * xphys + f * zspec
+    zc2r = 3 * zspec + 3 * phys
+    fwd = 3 * phys + 3 * zspec + (3 * zspec + 3 * xphys) + (3 * xphys + 3 * spec)
+    ab = bench.adjoint_bytes(n, 8, 4)
+    assert ab["spectral_1"] == 15 * spec                       # lam, mu in; G, lam, mu out
+    assert ab["inverse_u_omega"] == xinv(3, 6) + yinv(6) + 2 * zc2r
+    assert ab["inverse_G"] == xinv(3, 3) + yinv(3) + zc2r
+    assert ab["pointwise"] == 23 * phys                        # 13 physical fields in, 10 out
+    assert ab["forward_2x3"] == 2 * fwd
+    assert ab["spectral_2"] == 12 * spec                       # lam, Ub, Wb in; lam out
+    # the figures of the 512^3 launch list, in GB
+    got = {k: round(v / 1e9, 2) for k, v in ab.items()}
+    assert got == {"spectral_1": 2.39, "inverse_u_omega": 10.87, "inverse_G": 5.67, "pointwise": 12.35,
+                   "forward_2x3": 11.35, "spectral_2": 1.91}
