@@ -535,6 +535,8 @@ ps_status ps_init(const ps_params* p, void* cuda_stream, void* workspace_dev, si
     kp.K = 2 * mm + 1;
     kp.Kz = mmax_of(nz) + 1;
     const int Cw = tile_width(c->fp64);
+    // the same rounding as Geo<T, nz>::KZP: the kernels size their staging
+    // buffers with that compile-time width and stride lines by kp.Kzp
     kp.Kzp = (kp.Kz + Cw - 1) / Cw * Cw;
     kp.ks = 2.0 * M_PI / p->L;
     const double Lz = p->L * (double)nz / (double)n;
